@@ -1,0 +1,125 @@
+"""Writes tests/golden/cases.json: the lattice-unit constants of the five workloads (component
+constants, temperature, pressure, flash phase densities, volatility coefficients gamma_i and
+initial-profile geometry). Every number comes from the FP64 phase-equilibrium oracle
+(oracle/thermo.py) or from the seeded input module; nothing here calls the CUDA library.
+
+Run:  python tests/golden/make_cases.py
+
+Workload choices where the paper is silent:
+  * T = 0.85 * T_pc (T_pc = sum_i z_i T_ci) for the slab, droplet and sphere cases; the batched
+    sweep draws T / T_pc uniformly in [0.75, 0.95].
+  * The pressure is the one at which the flash's liquid volume fraction equals the geometric
+    liquid fraction of the initial profile (1/2 for a half-domain slab, pi R^2 / L^2 for a disc,
+    4/3 pi R^3 / L^3 for a sphere), so that the overall feed of the lattice is close to z.
+  * beta = 1.945 for slabs (Section 4.2) and 1.915 for droplets (Section 4.3); G = -1;
+    tau = 0.8 (Section 4.2) unless the workload states otherwise; interface width W = 4.
+  * MRT rates: 1/tau on the momentum and stress rows, 1.0 on energy / energy-square rows,
+    1.2 on the heat-flux (and D3Q19 ghost) rows, 1.0 on the D3Q19 pi rows.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import lbm_inputs  # noqa: E402
+from oracle import thermo as th  # noqa: E402
+
+K_TO_R = 1.8
+PSIA_TO_MPA = 0.00689475729
+
+# Critical constants: C1 and nC4 as stated for the workloads; C3 and nC5 from Table 1
+# (psia, degrees Rankine) converted to MPa and K.
+C1 = th.Component("C1", 190.6, 4.60, 0.011, 16.043)
+NC4 = th.Component("nC4", 425.1, 3.80, 0.200, 58.123)
+C3 = th.Component("C3", 666.06 / K_TO_R, 616.00 * PSIA_TO_MPA, 0.152, 44.097)
+NC5 = th.Component("nC5", 845.80 / K_TO_R, 488.60 * PSIA_TO_MPA, 0.251, 72.150)
+
+
+def mrt_rates(Q, tau):
+    s = 1.0 / tau
+    if Q == 9:  # rho, e, eps, jx, qx, jy, qy, pxx, pxy
+        return [s, 1.0, 1.0, s, 1.2, s, 1.2, s, s]
+    # rho, e, eps, jx, qx, jy, qy, jz, qz, 3pxx, 3pixx, pww, piww, pxy, pyz, pxz, mx, my, mz
+    return [s, 1.0, 1.0, s, 1.2, s, 1.2, s, 1.2, s, 1.0, s, 1.0, s, s, s, 1.2, 1.2, 1.2]
+
+
+def thermo_case(phys, z, tfrac, liquid_fraction, kij=None):
+    comps, ts, ps = th.lattice_components(phys)
+    nc = len(comps)
+    kij = kij or [[0.0] * nc for _ in range(nc)]
+    Tpc = sum(zi * c.Tc for zi, c in zip(z, comps))
+    T = tfrac * Tpc
+    p, fr = th.pressure_for_liquid_fraction(comps, kij, T, z, liquid_fraction)
+    rl, rv, nl, nv = th.phase_partial_densities(comps, T, p, 1.0, fr)
+    gamma, h = th.gamma_coefficients(rl, rv, fr.K)
+    return dict(
+        components=[dict(name=c.name, Tc=c.Tc, pc=c.pc, omega=c.omega, M=c.M) for c in comps],
+        z=list(z), T=T, T_over_Tpc=tfrac, p=p, p_phys_MPa=p / ps, T_phys_K=T / ts,
+        x=list(fr.x), y=list(fr.y), Zl=fr.Zl, Zv=fr.Zv, V=fr.V, K=list(fr.K),
+        rho_l=[float(v) for v in rl], rho_v=[float(v) for v in rv],
+        n_l=nl, n_v=nv, gamma=list(gamma), least_volatile=h, kij=kij,
+        residual=fr.residual, G=-1.0)
+
+
+def main():
+    seed = lbm_inputs.DEFAULT_SEED
+    cases = {}
+
+    c = thermo_case([C1, NC4], [0.3, 0.7], 0.85, 0.5)
+    c.update(name="slab_d2q9_fp64_bgk", Q=9, shape=[64, 64], tau=1.0, beta=1.945,
+             collision="bgk", precision="fp64", steps=2000,
+             init=dict(kind="slab", axis="y", lo=15.5, hi=47.5, width=4.0, noise=0.01, seed=seed))
+    cases["c1"] = c
+
+    radius = lbm_inputs.droplet_radius(seed)
+    c = thermo_case([C1, C3, NC5], [0.2, 0.3, 0.5], 0.85, math.pi * radius ** 2 / 512 ** 2)
+    c.update(name="droplet_d2q9_fp32s_mrt", Q=9, shape=[512, 512], tau=0.8, beta=1.915,
+             collision="mrt", mrt_s=mrt_rates(9, 0.8), precision="fp32s", steps=20000,
+             init=dict(kind="ball", radius=radius, width=4.0))
+    cases["c2"] = c
+
+    c = thermo_case([C1, C3, NC5], [0.2, 0.3, 0.5], 0.85, 4.0 / 3.0 * math.pi * 48 ** 3 / 256 ** 3)
+    c.update(name="sphere_d3q19_fp32s_mrt", Q=19, shape=[256, 256, 256], tau=0.8, beta=1.915,
+             collision="mrt", mrt_s=mrt_rates(19, 0.8), precision="fp32s", steps=5000,
+             init=dict(kind="ball", radius=48.0, width=4.0))
+    cases["c3"] = c
+
+    c = thermo_case([C1, NC4], [0.3, 0.7], 0.85, math.pi * 64 ** 2 / 256 ** 2)
+    c.update(name="droplet_d2q9_fp32s_bgk_adjoint", Q=9, shape=[256, 256], tau=0.8, beta=1.915,
+             collision="bgk", precision="fp32s", steps=3000, checkpoint_every=55,
+             target_k12=0.02, init=dict(kind="ball", radius=64.0, width=4.0))
+    cases["c5"] = c
+
+    def feasible(d):
+        try:
+            thermo_case([C1, NC4], [d[2], 1 - d[2]], d[1], 0.5)
+            return True
+        except ValueError:
+            return False
+
+    draws = lbm_inputs.batch_case_draws(512, seed + 4, accept=feasible)
+    batch = []
+    for k, (lx, tfrac, z1) in enumerate(draws):
+        c = thermo_case([C1, NC4], [z1, 1 - z1], tfrac, 0.5)
+        c.update(shape=[lx, 8],
+                 init=dict(kind="slab", axis="x", lo=lx / 4.0 - 0.5, hi=3 * lx / 4.0 - 0.5,
+                           width=4.0, noise=0.01, seed=seed + 1000 + k))
+        batch.append(c)
+        if k % 64 == 0:
+            print("batch case", k, lx, round(tfrac, 4), round(z1, 4), flush=True)
+    cases["c4"] = dict(name="batched_flash_d2q9_fp32s_bgk", Q=9, tau=0.8, beta=1.945,
+                       collision="bgk", precision="fp32s", steps=10000, cases=batch)
+
+    with open(os.path.join(HERE, "cases.json"), "w") as fh:
+        json.dump(cases, fh, indent=1)
+    print("wrote", os.path.join(HERE, "cases.json"))
+
+
+if __name__ == "__main__":
+    main()
