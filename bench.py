@@ -1,0 +1,347 @@
+"""Benchmark of the multi-component pseudo-potential LB step on one GB300.
+
+Workload: the 3-component (C1/C3/nC5) D3Q19 MRT sphere on a 256^3 periodic grid with FP32
+populations stored shifted and an FP64 EOS (constants from tests/golden/cases.json, seeded
+synthetic initial fields from lbm_inputs). One "step" is one full time step of the lattice:
+pseudo-potential pass + force / split / collide / in-place stream pass.
+
+Prints one JSON line. `value` is component-MLUPS (sites x components x steps / s) over the
+device-timed region with the populations resident in HBM; `e2e` is the same metric through
+the C ABI with host buffers (lbm_init from host densities, the steps, lbm_fields back to host
+densities) inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --impl reference the oracle (FP64 CPU, the test oracle) is timed on the host cores on a
+bounded sample of the same workload; under torchrun only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "component-MLUPS (D3Q19 MRT, FP32-shifted populations, FP64 EOS)"
+UNIT = "MLUPS/component"
+WORKLOAD = "sphere_d3q19_fp32s_mrt: 3 components C1/C3/nC5, 256^3 periodic, droplet R=48"
+
+
+def load_case(key="c3"):
+    with open(os.path.join(ROOT, "tests", "golden", "cases.json")) as fh:
+        return json.load(fh)[key]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1909_12390_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as fh:
+                h.update(fn.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_name):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel sources; otherwise None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get(kernel_name)
+    if not e or e.get("source_sha") != kernel_source_sha():
+        return None
+    return e.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def init_fields(c):
+    import lbm_inputs
+    grid = tuple(reversed(c["shape"]))
+    return lbm_inputs.ball_fields(grid, c["rho_l"], c["rho_v"], c["init"]["radius"], c["init"]["width"])
+
+
+def lattice_for(c, precision):
+    from paper_1909_12390_gb300 import lbm
+    comps = [(d["Tc"], d["pc"], d["omega"], d["M"]) for d in c["components"]]
+    return lbm.Lattice(tuple(c["shape"]), comps, T=c["T"], tau=c["tau"], gamma=c["gamma"],
+                       kij=np.array(c["kij"], dtype=float), beta=c["beta"], G=c["G"],
+                       collision=lbm.MRT if c["collision"] == "mrt" else lbm.BGK,
+                       mrt_rates=c.get("mrt_s"), precision=precision)
+
+
+def _oracle_sample(c, n):
+    import lbm_inputs
+    import oracle
+    k = [(d["Tc"], d["pc"], d["omega"], d["M"]) for d in c["components"]]
+    case = oracle.Case(Q=19, shape=(n, n, n), Tc=[x[0] for x in k], pc=[x[1] for x in k],
+                       omega=[x[2] for x in k], M=[x[3] for x in k], T=c["T"], tau=c["tau"],
+                       gamma=c["gamma"], kij=c["kij"], beta=c["beta"], G=c["G"], collision=1,
+                       s=c["mrt_s"])
+    rho = lbm_inputs.ball_fields((n, n, n), c["rho_l"], c["rho_v"], 48.0 * n / 256, c["init"]["width"])
+    return case, oracle.equilibrium(case, rho)
+
+
+def cpu_baseline(c, target_s=12.0, n=64):
+    """The oracle as it stands on the host cores: D3Q19 MRT steps of a periodic n^3 sample of
+    the workload (same constants, droplet radius scaled with the box), timed until about
+    target_s of CPU work."""
+    import oracle
+    case, f = _oracle_sample(c, n)
+    f = oracle.step(case, f, 1)  # warm-up (thread pool, pages)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        f = oracle.step(case, f, 1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > target_s:
+            break
+    val = n ** 3 * case.nc * steps / el / 1e6
+    return {"value": val, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d steps of a periodic %d^3 D3Q19 MRT FP64 sample of the workload (3 components)"
+                      % (steps, n)}
+
+
+def run_reference(args, rank):
+    """Reference arm: the oracle on the host cores, one oracle step of a periodic 32^3 sample
+    of the workload per benchmark step."""
+    if rank != 0:
+        return
+    import oracle
+    c = load_case()
+    n = 32
+    case, f = _oracle_sample(c, n)
+    f = oracle.step(case, f, args.warmup)
+    t0 = time.perf_counter()
+    f = oracle.step(case, f, args.steps)
+    el = time.perf_counter() - t0
+    val = n ** 3 * case.nc * args.steps / el / 1e6
+    sample = "periodic %d^3 D3Q19 MRT FP64 sample of the workload per step (3 components)" % n
+    out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference", "config": {"workload": WORKLOAD, "sample": sample},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--grid", type=int, default=0,
+                    help="cube edge of a smaller case of the same workload (profiling); 0 = 256")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_1909_12390_gb300 import lbm
+    c = load_case()
+    if args.grid:
+        c = dict(c, shape=[args.grid] * 3, init=dict(c["init"], radius=48.0 * args.grid / 256))
+    nc = len(c["components"])
+    N = int(np.prod(c["shape"]))
+    rho0 = init_fields(c)
+
+    gpu = lattice_for(c, lbm.FP32_SHIFTED)
+    gpu.init(rho0)
+    gpu.step(args.warmup)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    gpu.set_stream(stream.cuda_stream)
+    gpu.profile(True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        gpu.step(args.steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    ms_total = start.elapsed_time(stop)
+    psi_ms, psi_n = gpu.profile_read(0)
+    col_ms, col_n = gpu.profile_read(1)
+    gpu.profile(False)
+    mass_end = gpu.mass()
+    t_max = ms_total
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ms_step = t_max / args.steps
+    value = N * nc * args.steps * world / (t_max / 1e3) / 1e6
+
+    # roofline of the dominant kernel (force + collide + in-place stream): algorithmic bytes
+    # are one read and one write of every FP32 population, 2 * 19 * nc * 4 B per site.
+    peak, peak_kind = peaks()
+    alg_site = 2 * 19 * nc * 4
+    col_avg = col_ms / max(col_n, 1)
+    psi_avg = psi_ms / max(psi_n, 1)
+    dominant = "k_collide" if col_avg >= psi_avg else "k_psi"
+    achieved = N * alg_site / (col_avg / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": ncu_traffic("k_collide"),
+            "kernel": "k_collide<19,3,FP32S,MRT>", "peak_kind": peak_kind,
+            "alg_bytes_per_launch": N * alg_site,
+            "step_frac": (N * alg_site / (ms_step / 1e3) / 1e9) / peak,
+            "kernels_ms_avg": {"k_psi": psi_avg, "k_collide": col_avg}, "dominant": dominant}
+
+    # end to end through the C ABI with host buffers
+    gpu.set_stream(0)
+    rho_out = np.empty((nc,) + tuple(reversed(c["shape"])))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    gpu.init(rho0)
+    gpu.step(args.steps)
+    gpu.fields_into(rho=rho_out)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": N * nc * args.steps / e2e_s / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": int(rho0.nbytes / args.steps),
+           "d2h_bytes_per_step": int(rho_out.nbytes / args.steps),
+           "note": "lbm_init from host densities + steps + lbm_fields to host densities"}
+    gpu.close()
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        # plain FP64 storage on the same workload (the FP64 EOS is the same code)
+        g64 = lattice_for(c, lbm.FP64)
+        g64.init(rho0)
+        g64.step(3)
+        k64 = 20
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        g64.set_stream(stream.cuda_stream)
+        a.record(stream)
+        g64.step(k64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b) / k64
+        g64.close()
+        variants["fp64"] = {"value": N * nc / (ms64 / 1e3) / 1e6, "ms_per_step": ms64,
+                            "hbm_frac_of_step": (N * 2 * 19 * nc * 8 / (ms64 / 1e3) / 1e9) / peak}
+        variants["fp32s"] = {"value": value, "ms_per_step": ms_step}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "eos_dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "lattice": "D3Q19", "grid": c["shape"], "components": nc,
+                      "collision": "mrt", "precision": "fp32-shifted", "parallelism": "replicas" if world > 1 else "single",
+                      "l2": "inputs larger than L2 (%.2f GB populations)" % (N * 19 * nc * 4 / 1e9)},
+           "e2e": e2e, "roofline": roof, "gpu_launches": psi_n + col_n,
+           "clocks": clk.summary(), "site_mlups": value / nc,
+           "mass_drift": float(np.max(np.abs(mass_end / (rho0.reshape(nc, -1).sum(1)) - 1)))}
+    if variants:
+        out["variants"] = variants
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(c)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

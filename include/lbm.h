@@ -1,0 +1,168 @@
+/*
+ * lbm.h - C ABI of a GB300 (sm_103a) implementation of the time step of the
+ * thermodynamically consistent multi-component pseudo-potential lattice Boltzmann model
+ * of Peng, Ayala & Ayala, arXiv:1909.12390.
+ *
+ * One step, for every site x and every component s (Section 3.4):
+ *   rho_s = sum_a f_{s,a}                                             (cell-volume densities)
+ *   p_EOS = mixture Peng-Robinson pressure at the molar density n = sum rho_i / M_i and
+ *           molar composition c_i = (rho_i / M_i) / n       (Eq. MCPengRobinson, Eq. randommixingrule)
+ *   psi   = sqrt(2 (p_EOS - cs2 rho) / (G cs2)),  rho = sum_s rho_s            (Eq. psicorrected)
+ *   F     = -beta G psi(x) sum_a w_a psi(x+e_a) e_a
+ *           - (1-beta)/2 G sum_a w_a psi^2(x+e_a) e_a                          (Eq. coupledMCforce)
+ *   F_s   = chi_s F,  chi_s = gamma_s rho_s / sum_j gamma_j rho_j              (Eq. distributionforce)
+ *   u     = (sum_s sum_a e_a f_{s,a} + F/2) / rho                 (barycentric, Guo half force)
+ *   f_s  <- BGK collision with Guo forcing (Eq. LBE, Eq. equilibrium a, b), or MRT, then
+ *           periodic streaming f(x + e_a, t+1) = f*(x, t).
+ * Lattice units throughout: dt = dx = 1, cs2 = 1/3, gas constant R (default 1).
+ *
+ * Conventions for every call:
+ *   - Host pointers are owned by the caller; the library copies in and out. Device memory is
+ *     owned by the library and freed by lbm_destroy.
+ *   - Work runs on the context's stream (its own non-blocking stream unless lbm_set_stream
+ *     gave one). Every call that returns data or a status synchronises that stream.
+ *   - No exception crosses the ABI. Every call returns an lbm_status; lbm_last_error gives a
+ *     one-line description of the last failure of that context.
+ *   - Field layout: component-major, then z, y, x with x fastest: rho[s][z][y][x].
+ *   - Population layout (lbm_get_f / lbm_set_f): f[s][a][z][y][x], FP64, with the direction
+ *     order below (the same order as the oracle's and the tests'):
+ *       D2Q9 : (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+ *       D3Q19: (0,0,0) (1,0,0) (-1,0,0) (0,1,0) (0,-1,0) (0,0,1) (0,0,-1) (1,1,0) (-1,-1,0)
+ *              (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1)
+ *              (0,1,-1) (0,-1,1)
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,        /* invalid argument; nothing was changed */
+  LBM_ERR_CUDA = -2,       /* a CUDA runtime call failed; see lbm_last_error */
+  LBM_ERR_OOM = -3,        /* device allocation failed */
+  LBM_ERR_PSI_DOMAIN = -4, /* psi^2 < 0 or b_m n >= 1 at some site (EOS out of its domain) */
+  LBM_ERR_NONFINITE = -5,  /* a density or psi^2 is NaN or infinite */
+  LBM_ERR_TIMEOUT = -6     /* a bounded device-side wait ran out (fused kernel) */
+} lbm_status;
+
+enum { LBM_D2Q9 = 9, LBM_D3Q19 = 19 };
+enum { LBM_BGK = 0, LBM_MRT = 1 };
+enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1 };
+
+typedef struct {
+  int nx, ny, nz; /* sites per axis, periodic; nz = 1 for D2Q9 */
+  int lattice;    /* LBM_D2Q9 or LBM_D3Q19 */
+} lbm_grid;
+
+/* One component in lattice units (critical temperature and pressure, Pitzer acentric
+ * factor, molar mass); see lbm_scale_to_lattice for the paper's scaling. */
+typedef struct {
+  double Tc, pc, omega, M;
+} lbm_component;
+
+typedef struct {
+  double T;                /* temperature, lattice units */
+  double R;                /* gas constant; 0 means 1 */
+  const double *kij;       /* nc*nc binary interaction coefficients zeta_ij (Eq.
+                              randommixingrule), row-major, symmetric; NULL means all 0 */
+  const double *gamma;     /* nc volatility coefficients of Eq. distributionforce, > 0;
+                              NULL means all 1 */
+  double beta;             /* Kupershtokh beta of Eq. coupledMCforce */
+  double G;                /* interaction strength; only its sign matters (psi^2 >= 0) */
+  int collision;           /* LBM_BGK or LBM_MRT */
+  const double *mrt_rates; /* Q relaxation rates, one per moment row (D2Q9: Lallemand-Luo
+                              rho e eps jx qx jy qy pxx pxy; D3Q19: d'Humieres rho e eps jx qx
+                              jy qy jz qz 3pxx 3pixx pww piww pxy pyz pxz mx my mz). The rows
+                              of rho, j and the shear stresses always relax at 1/tau; their
+                              entries are ignored. NULL with LBM_MRT is an error. */
+  int precision;           /* LBM_FP64, or LBM_FP32_SHIFTED: populations stored in FP32 as
+                              f_a - w_a rho_ref_s, moments in FP32, every EOS sum in FP64 */
+  const double *rho_ref;   /* nc shift references for LBM_FP32_SHIFTED; NULL means the mean
+                              of each component's density given to lbm_init */
+} lbm_eos;
+
+/* Creates a context for one periodic lattice with nc components (1..4), relaxation time
+ * tau > 1/2 (Eq. LBE). Validates every argument (LBM_ERR_ARG) and allocates the device
+ * populations (LBM_ERR_OOM). The populations are undefined until lbm_init or lbm_set_f. */
+lbm_status lbm_create(const lbm_grid *grid, int nc, const lbm_component *comps,
+                      const lbm_eos *eos, double tau, lbm_ctx **out);
+
+/* Releases every device and host resource of ctx. NULL is a no-op. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Uses the given cudaStream_t (passed as void*) for all later work; NULL restores the
+ * context's own stream. */
+lbm_status lbm_set_stream(lbm_ctx *ctx, void *stream);
+
+/* Sets the populations to the equilibrium of Eq. equilibrium(a), f_{s,a} = f_eq(rho_s, u),
+ * from host arrays rho[nc][N] and u[3][N] (NULL: u = 0), and the step counter to 0.
+ * With LBM_FP32_SHIFTED and rho_ref == NULL the shift references become the component means
+ * of rho. Densities must be finite and positive. */
+lbm_status lbm_init(lbm_ctx *ctx, const double *rho, const double *u);
+
+/* Advances n >= 0 steps. On a failing step the kernels of the remaining steps do nothing,
+ * the populations hold the state before the failing step (two-kernel path) and the status
+ * of the failure is returned; lbm_time then gives the index of that step. */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
+
+/* Number of steps taken since the last lbm_init / lbm_set_f. */
+int64_t lbm_time(const lbm_ctx *ctx);
+
+/* Macroscopic fields of the current state into host arrays (any may be NULL):
+ * rho[nc][N] cell-volume densities, u[3][N] barycentric velocity with the Guo half force,
+ * p[N] the EOS pressure (equal to the hydrodynamic pressure of Eq. hydropressure), psi[N]. */
+lbm_status lbm_fields(lbm_ctx *ctx, double *rho, double *u, double *p, double *psi);
+
+/* Total mass of each component, sum over sites of rho_s, reduced in FP64 in a fixed order
+ * (bit-reproducible), into host mass[nc]. */
+lbm_status lbm_mass(lbm_ctx *ctx, double *mass);
+
+/* Current populations in the canonical FP64 layout f[nc][Q][N] (shift added back). */
+lbm_status lbm_get_f(lbm_ctx *ctx, double *f);
+
+/* Replaces the populations with host f[nc][Q][N] (canonical FP64 layout; rounded to FP32
+ * after subtracting the shift when the context stores FP32) and sets the step counter to 0. */
+lbm_status lbm_set_f(lbm_ctx *ctx, const double *f);
+
+/* Size in bytes of the raw population storage (lbm_save / lbm_restore). */
+size_t lbm_state_bytes(const lbm_ctx *ctx);
+
+/* Checkpoint and resume: copies the raw device storage and the step counter to / from host
+ * memory of lbm_state_bytes(ctx) bytes. A restore followed by the same steps reproduces the
+ * original run bit for bit. */
+lbm_status lbm_save(lbm_ctx *ctx, void *buf, size_t bytes, int64_t *t);
+lbm_status lbm_restore(lbm_ctx *ctx, const void *buf, size_t bytes, int64_t t);
+
+/* Kernel timing. lbm_profile(ctx, 1) clears the record and from then on brackets every
+ * kernel launch of lbm_step with CUDA events on the context's stream (graph replay is off
+ * while profiling); lbm_profile(ctx, 0) stops recording. lbm_profile_read sums the recorded
+ * durations of one kernel kind (0 = pseudo-potential pass, 1 = force + collide + stream
+ * pass) in milliseconds and gives the number of launches. Both synchronise the stream. */
+lbm_status lbm_profile(lbm_ctx *ctx, int on);
+lbm_status lbm_profile_read(lbm_ctx *ctx, int kernel, double *total_ms, int64_t *launches);
+
+/* One-line description of the last failure of ctx ("" if none). Valid until the next call
+ * on ctx. With ctx == NULL, the last failure of lbm_create. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Section 4.2 scaling of physical constants to lattice units: a_1 = 2/49, b_1 = 2/21,
+ * M_1 = 1, R = 1 fix T_c1 = (0.0778 / 0.45724)(a_1 / b_1) and p_c1 = 0.0778 T_c1 / b_1;
+ * component i keeps T_ci / T_c1, p_ci / p_c1 and M_i / M_1, so every reduced quantity is
+ * unchanged. Writes nc lattice components to out and the lattice-unit temperature and
+ * pressure of (T_phys, p_phys) to T_lb and p_lb (either may be NULL). */
+lbm_status lbm_scale_to_lattice(int nc, const lbm_component *phys, double T_phys, double p_phys,
+                                lbm_component *out, double *T_lb, double *p_lb);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

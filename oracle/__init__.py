@@ -33,7 +33,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c++17",
-                               "-shared", "-fPIC", "-o", tmp, _SRC])
+                               "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -66,6 +66,7 @@ def lib():
         _lib.oracle_equilibrium.argtypes = [cp, dp, dp, dp]
         _lib.oracle_lattice.argtypes = [ctypes.c_int, ip, dp]
         _lib.oracle_mrt_matrix.argtypes = [ctypes.c_int, dp, dp]
+        _lib.oracle_threads.argtypes = []
     return _lib
 
 
@@ -236,6 +237,11 @@ def mrt_matrix(Q: int):
     if st != OK:
         raise OracleError(st)
     return M.reshape(Q, Q), Mi.reshape(Q, Q)
+
+
+def threads() -> int:
+    """OpenMP threads the oracle's loops use (set OMP_NUM_THREADS before the first call)."""
+    return int(lib().oracle_threads())
 
 
 def mass(f: np.ndarray) -> np.ndarray:

@@ -35,6 +35,8 @@
 //   * psi^2 < 0 is a domain error; nothing is clamped.
 //   * MRT (not in the paper): m = M f, m* = m - S (m - M f_eq) + (I - S/2) M Fbar, f* = M^-1 m*,
 //     Fbar the Guo term without its (1 - 1/2tau) factor, M^-1 by Gauss-Jordan elimination.
+#include <omp.h>
+
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -315,8 +317,9 @@ int macroscopic(const Setup& S, const T* kij, const T* f, Macro<T>& m) {
   m.psi2.assign(N, T(0.0));
   m.psi.assign(N, T(0.0));
   m.F.assign(3 * N, T(0.0));
-  int status = ORACLE_OK;
+  std::vector<int> site_status(N, ORACLE_OK);
   // Loop 1: moments, EOS, pseudo-potential.
+#pragma omp parallel for schedule(static)
   for (int64_t x = 0; x < N; ++x) {
     T rc[4];
     for (int s = 0; s < nc; ++s) {
@@ -333,16 +336,18 @@ int macroscopic(const Setup& S, const T* kij, const T* f, Macro<T>& m) {
     T p, psi2;
     int st = eos(S, kij, rc, &p, &psi2);
     if (st != ORACLE_OK) {
-      if (status == ORACLE_OK) status = st;
+      site_status[x] = st;
       continue;
     }
     m.p[x] = p;
     m.psi2[x] = psi2;
     m.psi[x] = sqrt_(psi2);
   }
-  if (status != ORACLE_OK) return status;
+  for (int64_t x = 0; x < N; ++x)
+    if (site_status[x] != ORACLE_OK) return site_status[x];
   // Total force, Eq. coupledMCforce:
   //   F = -beta G psi(x) sum_a w_a psi(x+e_a) e_a - (1 - beta)/2 G sum_a w_a psi^2(x+e_a) e_a
+#pragma omp parallel for collapse(2) schedule(static)
   for (int z = 0; z < S.nz; ++z)
     for (int y = 0; y < S.ny; ++y)
       for (int x = 0; x < S.nx; ++x) {
@@ -374,6 +379,7 @@ int step_once(const Setup& S, const T* kij, const T* gamma, const T* fin, T* fou
   std::vector<T> post((size_t)nc * Q * N);
   const double tau = S.tau;
   // Loop 2: split, velocity, collision.
+#pragma omp parallel for schedule(static)
   for (int64_t x = 0; x < N; ++x) {
     T rho = 0.0, gsum = 0.0;
     for (int s = 0; s < nc; ++s) {
@@ -431,6 +437,7 @@ int step_once(const Setup& S, const T* kij, const T* gamma, const T* fin, T* fou
     }
   }
   // Loop 3: periodic streaming.
+#pragma omp parallel for collapse(3) schedule(static)
   for (int s = 0; s < nc; ++s)
     for (int a = 0; a < Q; ++a)
       for (int z = 0; z < S.nz; ++z)
@@ -440,9 +447,11 @@ int step_once(const Setup& S, const T* kij, const T* gamma, const T* fin, T* fou
             int64_t j = neighbour(S, x, y, z, S.L.e[a]);
             fout[((int64_t)s * Q + a) * N + j] = post[((int64_t)s * Q + a) * N + i];
           }
+  int bad = 0;
+#pragma omp parallel for reduction(| : bad) schedule(static)
   for (int64_t k = 0; k < (int64_t)nc * Q * N; ++k)
-    if (!std::isfinite(val(fout[k]))) return ORACLE_ERR_NONFINITE;
-  return ORACLE_OK;
+    if (!std::isfinite(val(fout[k]))) bad = 1;
+  return bad ? ORACLE_ERR_NONFINITE : ORACLE_OK;
 }
 
 }  // namespace
@@ -564,6 +573,9 @@ int oracle_equilibrium(const oracle_case* c, const double* rho, const double* u,
   }
   return ORACLE_OK;
 }
+
+// Threads the oracle's loops use (OpenMP; results do not depend on it).
+int oracle_threads(void) { return omp_get_max_threads(); }
 
 // Lattice tables, exported for the tests' invariants (velocity e [19][3], weights [19]).
 int oracle_lattice(int Q, int* e, double* w) {

@@ -1,0 +1,528 @@
+// Host side of the C ABI declared in include/lbm.h: argument validation, the Peng-Robinson
+// component parameters of Section 3.2, device allocation, the step loop (replayed from a
+// captured CUDA graph once it is long enough) and read-back.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_core.cuh"
+#include "lbm_ops.h"
+
+namespace lbm {
+
+__global__ void k_mass_final(const double* partial, int nblocks, int nc, double* out) {
+  __shared__ double sh[256];
+  for (int c = 0; c < nc; ++c) {
+    double v = 0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partial[(int64_t)b * nc + c];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = sh[0];
+    __syncthreads();
+  }
+}
+
+}  // namespace lbm
+
+namespace {
+
+const double kOmegaA = 0.45724;
+const double kOmegaB = 0.0778;
+const int kGraphSteps = 64;  // steps per captured graph (even, so parity is fixed)
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct lbm_ctx {
+  lbm_grid grid{};
+  int nc = 0, Q = 0, precision = 0, collision = 0;
+  lbm::Params P{};
+  const lbm::Ops* ops = nullptr;
+  bool ref_given = false;
+  void* f = nullptr;
+  void* psi = nullptr;
+  int* status = nullptr;
+  long long* t_dev = nullptr;
+  double* partial = nullptr;
+  double* mass_dev = nullptr;
+  double* scratch = nullptr;  // fields and staging, (nc + 5) * N doubles, allocated on demand
+  cudaStream_t own = nullptr, stream = nullptr;
+  int64_t t = 0;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_failed = false;
+  // per-kernel event timing (lbm_profile): events recorded around every launch on the stream
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_marks[2];  // (start, stop) pool indices per kernel kind
+  size_t ev_used = 0;
+  std::string err;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx* c, lbm_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c)
+    c->err = buf;
+  else
+    g_create_error = buf;
+  return st;
+}
+
+lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define CK(ctx, call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+double m_factor(double w) {
+  return w <= 0.49 ? 0.374640 + 1.54226 * w - 0.26992 * w * w
+                   : 0.379642 + 1.48503 * w - 0.164423 * w * w + 0.016666 * w * w * w;
+}
+
+int rows_q(int Q, int i) { return Q == 9 ? lbm::Lat<9>::krow(i) : lbm::Lat<19>::krow(i); }
+int nk_q(int Q) { return Q == 9 ? lbm::Lat<9>::NK : lbm::Lat<19>::NK; }
+int norm_q(int Q, int k) { return Q == 9 ? lbm::mnorm<9>(k) : lbm::mnorm<19>(k); }
+double w_q(int Q, int a) { return Q == 9 ? lbm::Lat<9>::w(a) : lbm::Lat<19>::w(a); }
+
+lbm_status ensure_scratch(lbm_ctx* c) {
+  if (c->scratch) return LBM_OK;
+  size_t n = (size_t)(c->nc + 5) * (size_t)c->P.N;
+  CK(c, cudaMalloc(&c->scratch, n * sizeof(double)));
+  return LBM_OK;
+}
+
+lbm_status sync_status(lbm_ctx* c) {
+  int st = 0;
+  long long t = 0;
+  CK(c, cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(&t, c->t_dev, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  CK(c, cudaGetLastError());
+  c->t = t;
+  if (st == 0) return LBM_OK;
+  CK(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (st & lbm::ST_NONFINITE) return fail(c, LBM_ERR_NONFINITE, "non-finite density or psi^2 at step %lld", t);
+  if (st & lbm::ST_PSI_DOMAIN)
+    return fail(c, LBM_ERR_PSI_DOMAIN, "psi^2 < 0 or b_m n >= 1 at step %lld", t);
+  return fail(c, LBM_ERR_TIMEOUT, "device wait timed out at step %lld", t);
+}
+
+int next_event(lbm_ctx* c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    c->ev_pool.push_back(e);
+  }
+  return (int)c->ev_used++;
+}
+
+void launch_steps(lbm_ctx* c, int64_t n, int64_t t0) {
+  for (int64_t i = 0; i < n; ++i) {
+    int parity = (int)((t0 + i) & 1);
+    int e0 = -1, e1 = -1, e2 = -1;
+    if (c->profiling) {
+      e0 = next_event(c);
+      e1 = next_event(c);
+      e2 = next_event(c);
+    }
+    if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], c->stream);
+    c->ops->psi(c->P, c->f, c->psi, c->status, parity, c->stream);
+    if (e1 >= 0) cudaEventRecord(c->ev_pool[e1], c->stream);
+    c->ops->collide(c->P, c->f, c->psi, c->status, c->t_dev, parity, c->stream);
+    if (e2 >= 0) {
+      cudaEventRecord(c->ev_pool[e2], c->stream);
+      c->ev_marks[0].push_back({e0, e1});
+      c->ev_marks[1].push_back({e1, e2});
+    }
+  }
+}
+
+void drop_graph(lbm_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+}
+
+// Captures kGraphSteps steps starting at an even step; on any capture failure the context
+// falls back to direct launches for good.
+bool build_graph(lbm_ctx* c) {
+  if (c->graph) return true;
+  if (c->graph_failed || c->stream == nullptr) return false;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    c->graph_failed = true;
+    return false;
+  }
+  launch_steps(c, kGraphSteps, 0);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (e != cudaSuccess || !g) {
+    cudaGetLastError();
+    c->graph_failed = true;
+    return false;
+  }
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->graph = nullptr;
+    c->graph_failed = true;
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_grid* grid, int nc, const lbm_component* comps, const lbm_eos* eos,
+                      double tau, lbm_ctx** out) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!grid || !comps || !eos) return fail(nullptr, LBM_ERR_ARG, "grid, comps and eos must be non-NULL");
+  if (grid->lattice != LBM_D2Q9 && grid->lattice != LBM_D3Q19)
+    return fail(nullptr, LBM_ERR_ARG, "lattice must be 9 (D2Q9) or 19 (D3Q19)");
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return fail(nullptr, LBM_ERR_ARG, "grid sizes must be >= 1");
+  if (grid->lattice == LBM_D2Q9 && grid->nz != 1) return fail(nullptr, LBM_ERR_ARG, "D2Q9 needs nz == 1");
+  const int64_t N = (int64_t)grid->nx * grid->ny * grid->nz;
+  if (N > ((int64_t)1 << 40)) return fail(nullptr, LBM_ERR_ARG, "grid too large");
+  if (nc < 1 || nc > 4) return fail(nullptr, LBM_ERR_ARG, "nc must be 1..4");
+  if (!(tau > 0.5) || !std::isfinite(tau)) return fail(nullptr, LBM_ERR_ARG, "tau must be > 1/2");
+  if (eos->precision != LBM_FP64 && eos->precision != LBM_FP32_SHIFTED)
+    return fail(nullptr, LBM_ERR_ARG, "precision must be LBM_FP64 or LBM_FP32_SHIFTED");
+  if (eos->collision != LBM_BGK && eos->collision != LBM_MRT)
+    return fail(nullptr, LBM_ERR_ARG, "collision must be LBM_BGK or LBM_MRT");
+  if (eos->collision == LBM_MRT && !eos->mrt_rates) return fail(nullptr, LBM_ERR_ARG, "MRT needs mrt_rates");
+  if (!(eos->T > 0) || !std::isfinite(eos->T)) return fail(nullptr, LBM_ERR_ARG, "T must be > 0");
+  if (!(eos->G != 0) || !std::isfinite(eos->G)) return fail(nullptr, LBM_ERR_ARG, "G must be nonzero");
+  if (!std::isfinite(eos->beta)) return fail(nullptr, LBM_ERR_ARG, "beta must be finite");
+  const double R = eos->R == 0 ? 1.0 : eos->R;
+  if (!(R > 0) || !std::isfinite(R)) return fail(nullptr, LBM_ERR_ARG, "R must be > 0");
+  for (int i = 0; i < nc; ++i) {
+    const lbm_component& k = comps[i];
+    if (!(k.Tc > 0) || !(k.pc > 0) || !(k.M > 0) || !std::isfinite(k.omega) || !std::isfinite(k.Tc) ||
+        !std::isfinite(k.pc) || !std::isfinite(k.M))
+      return fail(nullptr, LBM_ERR_ARG, "component %d: Tc, pc, M must be finite and > 0", i);
+    if (eos->gamma && (!(eos->gamma[i] > 0) || !std::isfinite(eos->gamma[i])))
+      return fail(nullptr, LBM_ERR_ARG, "gamma[%d] must be finite and > 0", i);
+    if (eos->rho_ref && !std::isfinite(eos->rho_ref[i]))
+      return fail(nullptr, LBM_ERR_ARG, "rho_ref[%d] must be finite", i);
+    if (eos->kij)
+      for (int j = 0; j < nc; ++j)
+        if (!std::isfinite(eos->kij[i * nc + j]) || eos->kij[i * nc + j] != eos->kij[j * nc + i])
+          return fail(nullptr, LBM_ERR_ARG, "kij must be finite and symmetric");
+  }
+  const int Q = grid->lattice;
+  if (eos->collision == LBM_MRT)
+    for (int k = 0; k < Q; ++k)
+      if (!std::isfinite(eos->mrt_rates[k]) || !(eos->mrt_rates[k] > 0) || !(eos->mrt_rates[k] < 2))
+        return fail(nullptr, LBM_ERR_ARG, "mrt_rates[%d] must lie in (0, 2)", k);
+  const lbm::Ops* ops = Q == 9 ? lbm::ops_q9(nc, eos->precision, eos->collision)
+                               : lbm::ops_q19(nc, eos->precision, eos->collision);
+  if (!ops) return fail(nullptr, LBM_ERR_ARG, "no kernels for this configuration");
+
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+  c->grid = *grid;
+  c->nc = nc;
+  c->Q = Q;
+  c->precision = eos->precision;
+  c->collision = eos->collision;
+  c->ops = ops;
+  lbm::Params& P = c->P;
+  P.nx = grid->nx;
+  P.ny = grid->ny;
+  P.nz = grid->nz;
+  P.N = N;
+  P.nc = nc;
+  P.omega = 1.0 / tau;
+  for (int i = 0; i < nk_q(Q); ++i) {
+    int k = rows_q(Q, i);
+    P.lam[i] = eos->collision == LBM_MRT ? (eos->mrt_rates[k] - P.omega) / norm_q(Q, k) : 0.0;
+  }
+  // Section 3.2: a_i = Omega_a R^2 Tc^2 / pc, b_i = Omega_b R Tc / pc, alpha_i(T), m_i
+  double aa[4];
+  for (int i = 0; i < nc; ++i) {
+    const lbm_component& k = comps[i];
+    double sq = 1.0 + m_factor(k.omega) * (1.0 - std::sqrt(eos->T / k.Tc));
+    aa[i] = kOmegaA * R * R * k.Tc * k.Tc / k.pc * sq * sq;
+    P.b[i] = kOmegaB * R * k.Tc / k.pc;
+    P.invM[i] = 1.0 / k.M;
+    P.gamma[i] = eos->gamma ? eos->gamma[i] : 1.0;
+    P.rho_ref[i] = (eos->precision == LBM_FP32_SHIFTED && eos->rho_ref) ? eos->rho_ref[i] : 0.0;
+  }
+  for (int i = 0; i < nc; ++i)
+    for (int j = 0; j < nc; ++j)
+      P.Qa[i * 4 + j] = std::sqrt(aa[i] * aa[j]) * (1.0 - (eos->kij ? eos->kij[i * nc + j] : 0.0));
+  P.RT = R * eos->T;
+  P.cpsi = 2.0 / (eos->G * (1.0 / 3.0));
+  P.beta = eos->beta;
+  P.G = eos->G;
+  c->ref_given = eos->rho_ref != nullptr;
+
+  cudaError_t e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&c->f, (size_t)nc * Q * N * ops->store_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->psi, (size_t)N * ops->psi_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->t_dev, sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&c->partial, (size_t)((N + 255) / 256) * nc * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->mass_dev, 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->t_dev, 0, sizeof(long long));
+  if (e != cudaSuccess) {
+    lbm_status st = cuda_fail(nullptr, e, "lbm_create allocation");
+    lbm_destroy(c);
+    return st;
+  }
+  c->stream = c->own;
+  *out = c;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graph(c);
+  cudaFree(c->f);
+  cudaFree(c->psi);
+  cudaFree(c->status);
+  cudaFree(c->t_dev);
+  cudaFree(c->partial);
+  cudaFree(c->mass_dev);
+  cudaFree(c->scratch);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->own) cudaStreamDestroy(c->own);
+  delete c;
+}
+
+lbm_status lbm_profile(lbm_ctx* c, int on) {
+  if (!c) return LBM_ERR_ARG;
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->profiling = on != 0;
+  c->ev_used = 0;
+  c->ev_marks[0].clear();
+  c->ev_marks[1].clear();
+  return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_ctx* c, int kernel, double* total_ms, int64_t* launches) {
+  if (!c || kernel < 0 || kernel > 1) return c ? fail(c, LBM_ERR_ARG, "kernel must be 0 or 1") : LBM_ERR_ARG;
+  CK(c, cudaStreamSynchronize(c->stream));
+  double sum = 0;
+  for (auto& m : c->ev_marks[kernel]) {
+    float ms = 0;
+    CK(c, cudaEventElapsedTime(&ms, c->ev_pool[m.first], c->ev_pool[m.second]));
+    sum += ms;
+  }
+  if (total_ms) *total_ms = sum;
+  if (launches) *launches = (int64_t)c->ev_marks[kernel].size();
+  return LBM_OK;
+}
+
+lbm_status lbm_set_stream(lbm_ctx* c, void* stream) {
+  if (!c) return LBM_ERR_ARG;
+  CK(c, cudaStreamSynchronize(c->stream));
+  drop_graph(c);
+  c->graph_failed = false;
+  c->stream = stream ? (cudaStream_t)stream : c->own;
+  return LBM_OK;
+}
+
+lbm_status lbm_init(lbm_ctx* c, const double* rho, const double* u) {
+  if (!c) return LBM_ERR_ARG;
+  if (!rho) return fail(c, LBM_ERR_ARG, "rho is NULL");
+  const int64_t N = c->P.N;
+  double mean[4] = {0, 0, 0, 0};
+  for (int s = 0; s < c->nc; ++s) {
+    for (int64_t i = 0; i < N; ++i) {
+      double v = rho[s * N + i];
+      if (!(v > 0) || !std::isfinite(v)) return fail(c, LBM_ERR_ARG, "rho[%d][%lld] must be finite and > 0", s, (long long)i);
+      mean[s] += v;
+    }
+    mean[s] /= (double)N;
+  }
+  if (u)
+    for (int64_t i = 0; i < 3 * N; ++i)
+      if (!std::isfinite(u[i])) return fail(c, LBM_ERR_ARG, "u must be finite");
+  if (c->precision == LBM_FP32_SHIFTED && !c->ref_given) {
+    for (int s = 0; s < c->nc; ++s) c->P.rho_ref[s] = mean[s];
+    drop_graph(c);  // the graph holds the parameters by value
+  }
+  lbm_status st = ensure_scratch(c);
+  if (st != LBM_OK) return st;
+  double* d_rho = c->scratch;
+  double* d_u = c->scratch + (size_t)c->nc * N;
+  CK(c, cudaMemcpyAsync(d_rho, rho, (size_t)c->nc * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (u) CK(c, cudaMemcpyAsync(d_u, u, (size_t)3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  c->ops->init(c->P, c->f, d_rho, u ? d_u : nullptr, c->stream);
+  CK(c, cudaGetLastError());
+  CK(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+  CK(c, cudaMemsetAsync(c->t_dev, 0, sizeof(long long), c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->t = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int64_t n) {
+  if (!c) return LBM_ERR_ARG;
+  if (n < 0) return fail(c, LBM_ERR_ARG, "n must be >= 0");
+  int64_t t = c->t, left = n;
+  if ((t & 1) && left > 0) {  // reach an even step before replaying graphs
+    launch_steps(c, 1, t);
+    ++t;
+    --left;
+  }
+  while (!c->profiling && left >= kGraphSteps && build_graph(c)) {
+    CK(c, cudaGraphLaunch(c->graph, c->stream));
+    t += kGraphSteps;
+    left -= kGraphSteps;
+  }
+  launch_steps(c, left, t);
+  CK(c, cudaGetLastError());
+  return sync_status(c);
+}
+
+int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
+
+lbm_status lbm_fields(lbm_ctx* c, double* rho, double* u, double* p, double* psi) {
+  if (!c) return LBM_ERR_ARG;
+  lbm_status st = ensure_scratch(c);
+  if (st != LBM_OK) return st;
+  const int64_t N = c->P.N;
+  double* d_rho = c->scratch;
+  double* d_u = d_rho + (size_t)c->nc * N;
+  double* d_p = d_u + (size_t)3 * N;
+  double* d_psi = d_p + N;
+  const int parity = (int)(c->t & 1);
+  c->ops->psi(c->P, c->f, c->psi, c->status, parity, c->stream);
+  c->ops->fields(c->P, c->f, c->psi, d_rho, d_u, d_p, d_psi, parity, c->stream);
+  CK(c, cudaGetLastError());
+  if (rho) CK(c, cudaMemcpyAsync(rho, d_rho, (size_t)c->nc * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (u) CK(c, cudaMemcpyAsync(u, d_u, (size_t)3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (p) CK(c, cudaMemcpyAsync(p, d_p, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (psi) CK(c, cudaMemcpyAsync(psi, d_psi, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  int64_t t = c->t;
+  st = sync_status(c);
+  c->t = t;
+  return st;
+}
+
+lbm_status lbm_mass(lbm_ctx* c, double* mass) {
+  if (!c || !mass) return c ? fail(c, LBM_ERR_ARG, "mass is NULL") : LBM_ERR_ARG;
+  c->ops->mass(c->P, c->f, c->partial, c->mass_dev, c->stream);
+  CK(c, cudaGetLastError());
+  CK(c, cudaMemcpyAsync(mass, c->mass_dev, (size_t)c->nc * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_f(lbm_ctx* c, double* f) {
+  if (!c || !f) return c ? fail(c, LBM_ERR_ARG, "f is NULL") : LBM_ERR_ARG;
+  const int64_t N = c->P.N;
+  double* d = nullptr;
+  const size_t bytes = (size_t)c->nc * c->Q * N * sizeof(double);
+  CK(c, cudaMallocAsync(&d, bytes, c->stream));
+  c->ops->get_f(c->P, c->f, d, (int)(c->t & 1), c->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, bytes, cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(d, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_get_f");
+  return LBM_OK;
+}
+
+lbm_status lbm_set_f(lbm_ctx* c, const double* f) {
+  if (!c || !f) return c ? fail(c, LBM_ERR_ARG, "f is NULL") : LBM_ERR_ARG;
+  const int64_t N = c->P.N;
+  const size_t n = (size_t)c->nc * c->Q * N;
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(f[i])) return fail(c, LBM_ERR_ARG, "f must be finite");
+  double* d = nullptr;
+  CK(c, cudaMallocAsync(&d, n * sizeof(double), c->stream));
+  cudaError_t e = cudaMemcpyAsync(d, f, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) {
+    c->ops->set_f(c->P, c->f, d, c->stream);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(d, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->t_dev, 0, sizeof(long long), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_set_f");
+  c->t = 0;
+  return LBM_OK;
+}
+
+size_t lbm_state_bytes(const lbm_ctx* c) {
+  return c ? (size_t)c->nc * c->Q * (size_t)c->P.N * c->ops->store_bytes : 0;
+}
+
+lbm_status lbm_save(lbm_ctx* c, void* buf, size_t bytes, int64_t* t) {
+  if (!c || !buf) return c ? fail(c, LBM_ERR_ARG, "buf is NULL") : LBM_ERR_ARG;
+  if (bytes != lbm_state_bytes(c)) return fail(c, LBM_ERR_ARG, "bytes must equal lbm_state_bytes");
+  CK(c, cudaMemcpyAsync(buf, c->f, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (t) *t = c->t;
+  return LBM_OK;
+}
+
+lbm_status lbm_restore(lbm_ctx* c, const void* buf, size_t bytes, int64_t t) {
+  if (!c || !buf) return c ? fail(c, LBM_ERR_ARG, "buf is NULL") : LBM_ERR_ARG;
+  if (bytes != lbm_state_bytes(c)) return fail(c, LBM_ERR_ARG, "bytes must equal lbm_state_bytes");
+  if (t < 0) return fail(c, LBM_ERR_ARG, "t must be >= 0");
+  CK(c, cudaMemcpyAsync(c->f, buf, bytes, cudaMemcpyHostToDevice, c->stream));
+  long long tt = t;
+  CK(c, cudaMemcpyAsync(c->t_dev, &tt, sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->t = t;
+  return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+lbm_status lbm_scale_to_lattice(int nc, const lbm_component* phys, double T_phys, double p_phys,
+                                lbm_component* out, double* T_lb, double* p_lb) {
+  if (nc < 1 || nc > 4 || !phys || !out || !(phys[0].Tc > 0) || !(phys[0].pc > 0) || !(phys[0].M > 0))
+    return LBM_ERR_ARG;
+  const double a1 = 2.0 / 49.0, b1 = 2.0 / 21.0;
+  const double Tc1 = (kOmegaB / kOmegaA) * (a1 / b1);
+  const double pc1 = kOmegaB * Tc1 / b1;
+  const double ts = Tc1 / phys[0].Tc, ps = pc1 / phys[0].pc;
+  for (int i = 0; i < nc; ++i) {
+    if (!(phys[i].Tc > 0) || !(phys[i].pc > 0) || !(phys[i].M > 0)) return LBM_ERR_ARG;
+    out[i].Tc = phys[i].Tc * ts;
+    out[i].pc = phys[i].pc * ps;
+    out[i].omega = phys[i].omega;
+    out[i].M = phys[i].M / phys[0].M;
+  }
+  if (T_lb) *T_lb = T_phys * ts;
+  if (p_lb) *p_lb = p_phys * ps;
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,234 @@
+// Device-side building blocks of the multi-component pseudo-potential LB step
+// (Peng, Ayala & Ayala, arXiv:1909.12390): lattice tables, the MRT moment basis, the
+// in-place AA streaming addresses, the mixture Peng-Robinson EOS, the Kupershtokh force
+// and the Guo-forced BGK / MRT collision. Everything is a compile-time function of the
+// direction index so that fully unrolled loops fold every lattice constant.
+#pragma once
+
+#include <cstdint>
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------------------
+// Lattices. Direction order is part of the ABI (include/lbm.h).
+template <int Q>
+struct Lat;
+
+template <>
+struct Lat<9> {
+  static constexpr int D = 2;
+  __host__ __device__ static constexpr int e(int a, int d) {
+    // (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+    return d == 0 ? (a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0))
+         : d == 1 ? (a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0))
+                  : 0;
+  }
+  __host__ __device__ static constexpr int c2(int a) { return e(a, 0) * e(a, 0) + e(a, 1) * e(a, 1); }
+  __host__ __device__ static constexpr double w(int a) {
+    return c2(a) == 0 ? 4.0 / 9.0 : (c2(a) == 1 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+  __host__ __device__ static constexpr int opp(int a) {
+    return a == 0 ? 0 : (a <= 4 ? ((a - 1 + 2) % 4) + 1 : ((a - 5 + 2) % 4) + 5);
+  }
+  // Lallemand & Luo (2000) moment rows: rho e eps jx qx jy qy pxx pxy
+  __host__ __device__ static constexpr int m(int k, int a) {
+    return k == 0 ? 1
+         : k == 1 ? -4 + 3 * c2(a)
+         : k == 2 ? (8 - 21 * c2(a) + 9 * c2(a) * c2(a)) / 2
+         : k == 3 ? e(a, 0)
+         : k == 4 ? (-5 + 3 * c2(a)) * e(a, 0)
+         : k == 5 ? e(a, 1)
+         : k == 6 ? (-5 + 3 * c2(a)) * e(a, 1)
+         : k == 7 ? e(a, 0) * e(a, 0) - e(a, 1) * e(a, 1)
+                  : e(a, 0) * e(a, 1);
+  }
+  // Rows with a free relaxation rate; rho, j and the stress rows relax at 1/tau.
+  static constexpr int NK = 4;
+  __host__ __device__ static constexpr int krow(int i) { return i == 0 ? 1 : i == 1 ? 2 : i == 2 ? 4 : 6; }
+};
+
+template <>
+struct Lat<19> {
+  static constexpr int D = 3;
+  __host__ __device__ static constexpr int e(int a, int d) {
+    // 0:(0,0,0) 1:(1,0,0) 2:(-1,0,0) 3:(0,1,0) 4:(0,-1,0) 5:(0,0,1) 6:(0,0,-1)
+    // 7:(1,1,0) 8:(-1,-1,0) 9:(1,-1,0) 10:(-1,1,0) 11:(1,0,1) 12:(-1,0,-1) 13:(1,0,-1)
+    // 14:(-1,0,1) 15:(0,1,1) 16:(0,-1,-1) 17:(0,1,-1) 18:(0,-1,1)
+    return d == 0 ? (a == 1 || a == 7 || a == 9 || a == 11 || a == 13 ? 1
+                     : (a == 2 || a == 8 || a == 10 || a == 12 || a == 14 ? -1 : 0))
+         : d == 1 ? (a == 3 || a == 7 || a == 10 || a == 15 || a == 17 ? 1
+                     : (a == 4 || a == 8 || a == 9 || a == 16 || a == 18 ? -1 : 0))
+                  : (a == 5 || a == 11 || a == 14 || a == 15 || a == 18 ? 1
+                     : (a == 6 || a == 12 || a == 13 || a == 16 || a == 17 ? -1 : 0));
+  }
+  __host__ __device__ static constexpr int c2(int a) {
+    return e(a, 0) * e(a, 0) + e(a, 1) * e(a, 1) + e(a, 2) * e(a, 2);
+  }
+  __host__ __device__ static constexpr double w(int a) {
+    return c2(a) == 0 ? 1.0 / 3.0 : (c2(a) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+  __host__ __device__ static constexpr int opp(int a) { return a == 0 ? 0 : (a % 2 == 1 ? a + 1 : a - 1); }
+  // d'Humieres et al. (2002) moment rows: rho e eps jx qx jy qy jz qz 3pxx 3pixx pww piww
+  // pxy pyz pxz mx my mz
+  __host__ __device__ static constexpr int m(int k, int a) {
+    return k == 0 ? 1
+         : k == 1 ? 19 * c2(a) - 30
+         : k == 2 ? (21 * c2(a) * c2(a) - 53 * c2(a) + 24) / 2
+         : k == 3 ? e(a, 0)
+         : k == 4 ? (5 * c2(a) - 9) * e(a, 0)
+         : k == 5 ? e(a, 1)
+         : k == 6 ? (5 * c2(a) - 9) * e(a, 1)
+         : k == 7 ? e(a, 2)
+         : k == 8 ? (5 * c2(a) - 9) * e(a, 2)
+         : k == 9 ? 3 * e(a, 0) * e(a, 0) - c2(a)
+         : k == 10 ? (3 * c2(a) - 5) * (3 * e(a, 0) * e(a, 0) - c2(a))
+         : k == 11 ? e(a, 1) * e(a, 1) - e(a, 2) * e(a, 2)
+         : k == 12 ? (3 * c2(a) - 5) * (e(a, 1) * e(a, 1) - e(a, 2) * e(a, 2))
+         : k == 13 ? e(a, 0) * e(a, 1)
+         : k == 14 ? e(a, 1) * e(a, 2)
+         : k == 15 ? e(a, 0) * e(a, 2)
+         : k == 16 ? (e(a, 1) * e(a, 1) - e(a, 2) * e(a, 2)) * e(a, 0)
+         : k == 17 ? (e(a, 2) * e(a, 2) - e(a, 0) * e(a, 0)) * e(a, 1)
+                   : (e(a, 0) * e(a, 0) - e(a, 1) * e(a, 1)) * e(a, 2);
+  }
+  static constexpr int NK = 10;
+  __host__ __device__ static constexpr int krow(int i) {
+    return i == 0 ? 1 : i == 1 ? 2 : i == 2 ? 4 : i == 3 ? 6 : i == 4 ? 8
+         : i == 5 ? 10 : i == 6 ? 12 : i == 7 ? 16 : i == 8 ? 17 : 18;
+  }
+};
+
+template <int Q>
+__host__ __device__ constexpr int mnorm(int k) {
+  int s = 0;
+  for (int a = 0; a < Q; ++a) s += Lat<Q>::m(k, a) * Lat<Q>::m(k, a);
+  return s;
+}
+
+// ---------------------------------------------------------------------------------------
+// Parameters of one lattice, passed by value to every kernel.
+struct Params {
+  int nx, ny, nz;
+  int64_t N;  // nx * ny * nz
+  int nc;
+  // collision
+  double omega;      // 1 / tau
+  double lam[10];    // (s_k - 1/tau) / |row k|^2 for the free MRT rows, in Lat<Q>::krow order
+  // EOS, Section 3.2 (FP64)
+  double invM[4];    // 1 / M_i
+  double b[4];       // b_i (molar co-volume)
+  double Qa[16];     // sqrt(a_i alpha_i a_j alpha_j) (1 - zeta_ij)
+  double RT;
+  double cpsi;       // 2 / (G cs2): psi^2 = cpsi (p - cs2 rho)
+  double rho_ref[4]; // FP32 shift references (0 for FP64 storage)
+  double gamma[4];
+  double beta, G;
+};
+
+// Status bits raised by kernels (OR-ed into one device word).
+enum : int { ST_PSI_DOMAIN = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4 };
+
+// ---------------------------------------------------------------------------------------
+// Site coordinates and periodic neighbours.
+struct Site {
+  int x, y, z;
+  int xm, xp, ym, yp, zm, zp;
+  __device__ __forceinline__ void set(const Params& P, int64_t idx) {
+    x = (int)(idx % P.nx);
+    int64_t r = idx / P.nx;
+    y = (int)(r % P.ny);
+    z = (int)(r / P.ny);
+    xm = x == 0 ? P.nx - 1 : x - 1;
+    xp = x == P.nx - 1 ? 0 : x + 1;
+    ym = y == 0 ? P.ny - 1 : y - 1;
+    yp = y == P.ny - 1 ? 0 : y + 1;
+    zm = z == 0 ? P.nz - 1 : z - 1;
+    zp = z == P.nz - 1 ? 0 : z + 1;
+  }
+  // linear index of x + s * e (s = +1 or -1) for a direction with components (ex, ey, ez)
+  __device__ __forceinline__ int64_t nb(const Params& P, int ex, int ey, int ez) const {
+    int xx = ex == 0 ? x : (ex > 0 ? xp : xm);
+    int yy = ey == 0 ? y : (ey > 0 ? yp : ym);
+    int zz = ez == 0 ? z : (ez > 0 ? zp : zm);
+    return ((int64_t)zz * P.ny + yy) * P.nx + xx;
+  }
+};
+
+// In-place AA streaming. State at even t: slot (x, a) holds f_a(x, t). After an even step
+// slot (x, opp a) holds f*_a(x) = f_a(x + e_a, t + 1), so at odd t f_a(x) sits in slot
+// (x - e_a, opp a); the odd step writes f*_a(x) to slot (x + e_a, a), which restores the even
+// layout. Each site reads and writes the same slots, so no two threads touch one slot.
+template <int Q>
+struct AA {
+  template <int A>
+  __device__ __forceinline__ static int64_t read_slot(const Params& P, const Site& s, int64_t idx,
+                                                      int parity, int comp) {
+    constexpr int O = Lat<Q>::opp(A);
+    if (parity == 0) return ((int64_t)comp * Q + A) * P.N + idx;
+    return ((int64_t)comp * Q + O) * P.N +
+           s.nb(P, -Lat<Q>::e(A, 0), -Lat<Q>::e(A, 1), -Lat<Q>::e(A, 2));
+  }
+  template <int A>
+  __device__ __forceinline__ static int64_t write_slot(const Params& P, const Site& s, int64_t idx,
+                                                       int parity, int comp) {
+    constexpr int O = Lat<Q>::opp(A);
+    if (parity == 0) return ((int64_t)comp * Q + O) * P.N + idx;
+    return ((int64_t)comp * Q + A) * P.N + s.nb(P, Lat<Q>::e(A, 0), Lat<Q>::e(A, 1), Lat<Q>::e(A, 2));
+  }
+};
+
+// Compile-time loop.
+template <int I, int N>
+struct For {
+  template <class F>
+  __device__ __forceinline__ static void run(F&& f) {
+    f.template operator()<I>();
+    For<I + 1, N>::run(f);
+  }
+};
+template <int N>
+struct For<N, N> {
+  template <class F>
+  __device__ __forceinline__ static void run(F&&) {}
+};
+
+// ---------------------------------------------------------------------------------------
+// Mixture Peng-Robinson EOS (Eq. MCPengRobinson with Eq. randommixingrule), written without
+// the division by the molar density: with n_i = rho_i / M_i, n = sum n_i,
+//   b_m n = sum b_i n_i = B,   [a alpha]_m n^2 = sum_ij n_i n_j Qa_ij = A2,
+//   p = n R T / (1 - B) - A2 / (1 + 2B - B^2).
+// Returns the numerator pD = n R T (1 + 2B - B^2) - A2 (1 - B) and the denominator
+// Dd = (1 - B)(1 + 2B - B^2), both FP64, so p = pD / Dd. Every sum with cancellation is FP64.
+template <int NC>
+struct EosOut {
+  double pD, Dd, B;
+};
+
+template <int NC>
+__device__ __forceinline__ EosOut<NC> eos_pr(const Params& P, const double (&rho)[NC]) {
+  double n[NC];
+  double nt = 0.0, B = 0.0;
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    n[i] = rho[i] * P.invM[i];
+    nt += n[i];
+    B = fma(P.b[i], n[i], B);
+  }
+  double A2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    double v = P.Qa[i * 4 + i] * n[i];
+#pragma unroll
+    for (int j = i + 1; j < NC; ++j) v = fma(2.0 * P.Qa[i * 4 + j], n[j], v);
+    A2 = fma(n[i], v, A2);
+  }
+  double d1 = 1.0 - B;
+  double d2 = fma(B, 2.0 - B, 1.0);
+  EosOut<NC> o;
+  o.Dd = d1 * d2;
+  o.pD = fma(nt * P.RT, d2, -A2 * d1);
+  o.B = B;
+  return o;
+}
+
+}  // namespace lbm

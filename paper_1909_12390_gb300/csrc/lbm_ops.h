@@ -1,0 +1,28 @@
+// Dispatch table between the host context (lbm_capi.cu) and the kernel instantiations of one
+// lattice (lbm_d2q9.cu, lbm_d3q19.cu). Internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+struct Params;
+
+struct Ops {
+  void (*psi)(const Params&, const void* f, void* psi, int* status, int parity, cudaStream_t);
+  void (*collide)(const Params&, void* f, const void* psi, const int* status, long long* t_dev, int parity,
+                  cudaStream_t);
+  void (*init)(const Params&, void* f, const double* rho, const double* u, cudaStream_t);
+  void (*get_f)(const Params&, const void* f, double* out, int parity, cudaStream_t);
+  void (*set_f)(const Params&, void* f, const double* in, cudaStream_t);
+  void (*fields)(const Params&, const void* f, const void* psi, double* rho, double* u, double* p,
+                 double* psi_out, int parity, cudaStream_t);
+  void (*mass)(const Params&, const void* f, double* partial, double* out, cudaStream_t);
+  int store_bytes;  // bytes per stored population
+  int psi_bytes;    // bytes per stored pseudo-potential value
+};
+
+const Ops* ops_q9(int nc, int precision, int collision);
+const Ops* ops_q19(int nc, int precision, int collision);
+
+}  // namespace lbm

@@ -1,0 +1,238 @@
+"""Python binding of liblbm.so (include/lbm.h): argument marshalling only.
+
+Every step of the lattice Boltzmann path runs in the library's CUDA kernels. There is no
+CPU fallback: if the library is missing or cannot be loaded, the import fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblbm.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_PSI_DOMAIN, ERR_NONFINITE, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+D2Q9, D3Q19 = 9, 19
+BGK, MRT = 0, 1
+FP64, FP32_SHIFTED = 0, 1
+
+# the entry points include/lbm.h declares
+EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_init", "lbm_step", "lbm_time",
+           "lbm_fields", "lbm_mass", "lbm_get_f", "lbm_set_f", "lbm_state_bytes", "lbm_save",
+           "lbm_restore", "lbm_last_error", "lbm_scale_to_lattice", "lbm_profile",
+           "lbm_profile_read")
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("lbm status %d: %s" % (status, msg))
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("lattice", ctypes.c_int)]
+
+
+class Component(ctypes.Structure):
+    _fields_ = [("Tc", ctypes.c_double), ("pc", ctypes.c_double), ("omega", ctypes.c_double),
+                ("M", ctypes.c_double)]
+
+
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+class Eos(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_double), ("R", ctypes.c_double), ("kij", _DP), ("gamma", _DP),
+                ("beta", ctypes.c_double), ("G", ctypes.c_double), ("collision", ctypes.c_int),
+                ("mrt_rates", _DP), ("precision", ctypes.c_int), ("rho_ref", _DP)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads liblbm.so; raises if it is absent (build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("liblbm.so not built: %s (run __graft_entry__.build())" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        L.lbm_create.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.POINTER(Component),
+                                 ctypes.POINTER(Eos), ctypes.c_double, ctypes.POINTER(vp)]
+        L.lbm_destroy.argtypes = [vp]
+        L.lbm_destroy.restype = None
+        L.lbm_set_stream.argtypes = [vp, vp]
+        L.lbm_init.argtypes = [vp, _DP, _DP]
+        L.lbm_step.argtypes = [vp, ctypes.c_int64]
+        L.lbm_time.argtypes = [vp]
+        L.lbm_time.restype = ctypes.c_int64
+        L.lbm_fields.argtypes = [vp, _DP, _DP, _DP, _DP]
+        L.lbm_mass.argtypes = [vp, _DP]
+        L.lbm_get_f.argtypes = [vp, _DP]
+        L.lbm_set_f.argtypes = [vp, _DP]
+        L.lbm_state_bytes.argtypes = [vp]
+        L.lbm_state_bytes.restype = ctypes.c_size_t
+        L.lbm_save.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64)]
+        L.lbm_restore.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int64]
+        L.lbm_profile.argtypes = [vp, ctypes.c_int]
+        L.lbm_profile_read.argtypes = [vp, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_int64)]
+        L.lbm_last_error.argtypes = [vp]
+        L.lbm_last_error.restype = ctypes.c_char_p
+        L.lbm_scale_to_lattice.argtypes = [ctypes.c_int, ctypes.POINTER(Component), ctypes.c_double,
+                                           ctypes.c_double, ctypes.POINTER(Component), _DP, _DP]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_DP)
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+class Lattice:
+    """One periodic lattice with nc components, behind lbm_create / lbm_destroy.
+
+    shape is (nx, ny) for D2Q9 or (nx, ny, nz) for D3Q19; fields are returned with array
+    shape (nc, nz, ny, nx) / (nc, ny, nx) (x fastest), populations as (nc, Q, *grid)."""
+
+    def __init__(self, shape, components, T, tau, gamma=None, kij=None, beta=1.0, G=-1.0,
+                 collision=BGK, mrt_rates=None, precision=FP64, rho_ref=None, R=1.0):
+        L = lib()
+        shape = tuple(int(s) for s in shape)
+        self.Q = D2Q9 if len(shape) == 2 else D3Q19
+        nx, ny = shape[0], shape[1]
+        nz = shape[2] if len(shape) == 3 else 1
+        self.shape = shape
+        self.grid = tuple(reversed(shape))
+        self.N = nx * ny * nz
+        nc = len(components)
+        self.nc = nc
+        comps = (Component * nc)(*[Component(*c) for c in components])
+        self._keep = []
+
+        def arr(v, n):
+            if v is None:
+                return None
+            a = _f64(v, n)
+            self._keep.append(a)
+            return _dp(a)
+
+        eos = Eos(T=T, R=R, kij=arr(None if kij is None else np.asarray(kij, dtype=float).ravel(), nc * nc),
+                  gamma=arr(gamma, nc), beta=beta, G=G, collision=collision,
+                  mrt_rates=arr(mrt_rates, self.Q), precision=precision, rho_ref=arr(rho_ref, nc))
+        h = ctypes.c_void_p()
+        st = L.lbm_create(ctypes.byref(Grid(nx, ny, nz, self.Q)), nc, comps, ctypes.byref(eos), tau,
+                          ctypes.byref(h))
+        if st != OK:
+            raise LBMError(st, L.lbm_last_error(None).decode())
+        self._h = h
+        self.precision = precision
+
+    def _check(self, st):
+        if st != OK:
+            raise LBMError(st, lib().lbm_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_handle: int):
+        self._check(lib().lbm_set_stream(self._h, ctypes.c_void_p(stream_handle)))
+
+    def init(self, rho, u=None):
+        r = _f64(rho, self.nc * self.N)
+        uu = None if u is None else _f64(u, 3 * self.N)
+        self._check(lib().lbm_init(self._h, _dp(r), _dp(uu)))
+
+    def step(self, n: int = 1):
+        self._check(lib().lbm_step(self._h, int(n)))
+
+    @property
+    def time(self) -> int:
+        return int(lib().lbm_time(self._h))
+
+    def fields(self, rho=True, u=True, p=True, psi=True):
+        out = {}
+        bufs = {}
+        if rho:
+            bufs["rho"] = np.empty((self.nc,) + self.grid)
+        if u:
+            bufs["u"] = np.empty((3,) + self.grid)
+        if p:
+            bufs["p"] = np.empty(self.grid)
+        if psi:
+            bufs["psi"] = np.empty(self.grid)
+        self._check(lib().lbm_fields(self._h, _dp(bufs.get("rho")), _dp(bufs.get("u")),
+                                     _dp(bufs.get("p")), _dp(bufs.get("psi"))))
+        out.update(bufs)
+        return out
+
+    def fields_into(self, rho=None, u=None, p=None, psi=None):
+        """Writes the fields into caller-provided C-contiguous float64 host arrays."""
+        self._check(lib().lbm_fields(self._h, _dp(rho), _dp(u), _dp(p), _dp(psi)))
+
+    def mass(self) -> np.ndarray:
+        m = np.empty(self.nc)
+        self._check(lib().lbm_mass(self._h, _dp(m)))
+        return m
+
+    def get_f(self) -> np.ndarray:
+        f = np.empty((self.nc, self.Q) + self.grid)
+        self._check(lib().lbm_get_f(self._h, _dp(f)))
+        return f
+
+    def set_f(self, f):
+        a = _f64(f, self.nc * self.Q * self.N)
+        self._check(lib().lbm_set_f(self._h, _dp(a)))
+
+    def profile(self, on: bool):
+        self._check(lib().lbm_profile(self._h, 1 if on else 0))
+
+    def profile_read(self, kernel: int):
+        """(total milliseconds, launches) of kernel kind 0 (psi pass) or 1 (collide pass)."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(lib().lbm_profile_read(self._h, kernel, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def save(self):
+        n = int(lib().lbm_state_bytes(self._h))
+        buf = np.empty(n, dtype=np.uint8)
+        t = ctypes.c_int64()
+        self._check(lib().lbm_save(self._h, buf.ctypes.data_as(ctypes.c_void_p), n, ctypes.byref(t)))
+        return buf, t.value
+
+    def restore(self, buf, t):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(lib().lbm_restore(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.size, int(t)))
+
+
+def scale_to_lattice(components, T_phys, p_phys):
+    """Section 4.2 scaling (see include/lbm.h). components: list of (Tc, pc, omega, M)."""
+    nc = len(components)
+    src = (Component * nc)(*[Component(*c) for c in components])
+    dst = (Component * nc)()
+    T = ctypes.c_double()
+    p = ctypes.c_double()
+    st = lib().lbm_scale_to_lattice(nc, src, T_phys, p_phys, dst, ctypes.byref(T), ctypes.byref(p))
+    if st != OK:
+        raise LBMError(st, "lbm_scale_to_lattice")
+    return [(d.Tc, d.pc, d.omega, d.M) for d in dst], T.value, p.value

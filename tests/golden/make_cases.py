@@ -6,8 +6,12 @@ initial-profile geometry). Every number comes from the FP64 phase-equilibrium or
 Run:  python tests/golden/make_cases.py
 
 Workload choices where the paper is silent:
-  * T = 0.85 * T_pc (T_pc = sum_i z_i T_ci) for the slab, droplet and sphere cases; the batched
-    sweep draws T / T_pc uniformly in [0.75, 0.95].
+  * T = 0.85 * T_pc (T_pc = sum_i z_i T_ci) for the binary slab and droplet cases and
+    T = 0.90 * T_pc for the 3-component droplet and sphere; the batched sweep draws T / T_pc
+    uniformly in [0.75, 0.95]. At 0.85 T_pc the 3-component mixture has a phase-density ratio
+    of 43 and the converging pressure wave of the initial transient compresses the liquid core
+    of a 3-D droplet to b_m n -> 1 (the EOS's pole) within 20 steps in the oracle; at 0.90 the
+    ratio is 34 and the runs are stable.
   * The pressure is the one at which the flash's liquid volume fraction equals the geometric
     liquid fraction of the initial profile (1/2 for a half-domain slab, pi R^2 / L^2 for a disc,
     4/3 pi R^3 / L^3 for a sphere), so that the overall feed of the lattice is close to z.
@@ -78,13 +82,13 @@ def main():
     cases["c1"] = c
 
     radius = lbm_inputs.droplet_radius(seed)
-    c = thermo_case([C1, C3, NC5], [0.2, 0.3, 0.5], 0.85, math.pi * radius ** 2 / 512 ** 2)
+    c = thermo_case([C1, C3, NC5], [0.2, 0.3, 0.5], 0.90, math.pi * radius ** 2 / 512 ** 2)
     c.update(name="droplet_d2q9_fp32s_mrt", Q=9, shape=[512, 512], tau=0.8, beta=1.915,
              collision="mrt", mrt_s=mrt_rates(9, 0.8), precision="fp32s", steps=20000,
              init=dict(kind="ball", radius=radius, width=4.0))
     cases["c2"] = c
 
-    c = thermo_case([C1, C3, NC5], [0.2, 0.3, 0.5], 0.85, 4.0 / 3.0 * math.pi * 48 ** 3 / 256 ** 3)
+    c = thermo_case([C1, C3, NC5], [0.2, 0.3, 0.5], 0.90, 4.0 / 3.0 * math.pi * 48 ** 3 / 256 ** 3)
     c.update(name="sphere_d3q19_fp32s_mrt", Q=19, shape=[256, 256, 256], tau=0.8, beta=1.915,
              collision="mrt", mrt_s=mrt_rates(19, 0.8), precision="fp32s", steps=5000,
              init=dict(kind="ball", radius=48.0, width=4.0))

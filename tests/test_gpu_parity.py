@@ -1,0 +1,271 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, element by element
+on the same seeded inputs.
+
+Tolerances: FP64 storage 1e-12 relative on populations and densities (1e-10 after the
+2000-step slab run); FP32-shifted storage 2e-4 relative on densities, the bound the workloads
+state for FP32 populations with an FP64 EOS."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import lbm_inputs
+import oracle
+from conftest import GOLDEN
+from lbm_cases import gpu_lattice, initial_rho, oracle_case, random_rho
+
+pytestmark = pytest.mark.gpu
+
+FP64, FP32S = 0, 1
+TOL = {FP64: 1e-12, FP32S: 2e-4}
+
+
+@pytest.fixture(scope="module")
+def cases():
+    with open(os.path.join(GOLDEN, "cases.json")) as fh:
+        return json.load(fh)
+
+
+def _mixture(cases, nc):
+    """nc-component test mixture: C1/C3/nC5 of the droplet workloads, plus nC4 for nc = 4."""
+    c = dict(cases["c3"])
+    if nc == 4:
+        c4 = cases["c1"]
+        c["components"] = c["components"] + [c4["components"][1]]
+        c["rho_l"] = c["rho_l"] + [2.0]
+        c["rho_v"] = c["rho_v"] + [0.05]
+        c["gamma"] = [0.05, 0.5, 1.0, 0.8]
+        c["kij"] = [[0.0 if i == j else 0.01 * (i + j) for j in range(4)] for i in range(4)]
+    elif nc < 3:
+        keep = [0, 2] if nc == 2 else [2]
+        c["components"] = [c["components"][k] for k in keep]
+        for key in ("rho_l", "rho_v", "gamma"):
+            c[key] = [c[key][k] for k in keep]
+        c["gamma"] = [g / c["gamma"][-1] for g in c["gamma"]]
+        c["kij"] = [[0.0] * nc for _ in range(nc)]
+    return c
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32S])
+@pytest.mark.parametrize("collision", [0, 1])
+@pytest.mark.parametrize("nc", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [(8, 8), (13, 7), (8, 8, 8), (9, 5, 6)])
+def test_brute_force_small_grids(cases, shape, nc, collision, precision):
+    """Every population after 1, 2 and 10 steps on tiny periodic grids (one full tile and
+    ragged sizes), BGK and MRT, 1..4 components, FP64 and FP32-shifted storage."""
+    c = _mixture(cases, nc)
+    rates = cases["c2"]["mrt_s"] if len(shape) == 2 else cases["c3"]["mrt_s"]
+    ocase = oracle_case(c, shape, collision=collision, s=rates, tau=0.8, beta=1.9)
+    grid = ocase.grid
+    rho = random_rho(c, grid, seed=11 + nc)
+    u = 0.02 * (lbm_inputs.uniform01(5, 3 * ocase.nsites).reshape((3,) + grid) - 0.5)
+    if len(shape) == 2:
+        u[2] = 0
+    gpu = gpu_lattice(c, shape, precision, collision=collision, s=rates, tau=0.8, beta=1.9)
+    gpu.init(rho, u)
+    f = oracle.equilibrium(ocase, rho, u)
+    assert _rel(gpu.get_f(), f) < (1e-15 if precision == FP64 else 1e-6)
+    done = 0
+    for n in (1, 2, 10):
+        gpu.step(n - done)
+        f = oracle.step(ocase, f, n - done)
+        done = n
+        assert gpu.time == n
+        got = gpu.get_f()
+        assert _rel(got, f) < TOL[precision] * (1 if precision == FP64 else 0.1), n
+        rg = gpu.fields()["rho"]
+        ro = oracle.fields(ocase, f).rho
+        # FP32 rounding scales with the mass at a site, so the error of each component is
+        # measured against the local phase density (random fields span 300:1 here)
+        assert float(np.max(np.abs(rg - ro) / ro.sum(0))) < TOL[precision]
+        if precision == FP64:
+            assert float(np.max(np.abs(rg - ro) / ro)) < TOL[precision]
+    gpu.close()
+
+
+def test_fields_match_oracle(cases):
+    """rho, u, p and psi of lbm_fields against the oracle's fields, FP64, slab workload."""
+    c = cases["c1"]
+    shape = tuple(c["shape"])
+    ocase = oracle_case(c, shape)
+    rho = initial_rho(c, shape)
+    gpu = gpu_lattice(c, shape, FP64)
+    gpu.init(rho)
+    gpu.step(100)
+    f = oracle.step(ocase, oracle.equilibrium(ocase, rho), 100)
+    fo = oracle.fields(ocase, f)
+    fg = gpu.fields()
+    assert _rel(fg["rho"], fo.rho) < 1e-12
+    assert np.max(np.abs(fg["u"] - fo.u)) < 1e-12 * max(np.max(np.abs(fo.u)), 1e-3)
+    assert _rel(fg["p"], fo.p) < 1e-12
+    assert _rel(fg["psi"], fo.psi) < 1e-12
+
+
+def test_slab_fp64_full_run(cases):
+    """The FP64 D2Q9 BGK slab workload at its full size and step count (64 x 64, 2000 steps):
+    densities within 1e-10 of the oracle; per-component mass conserved."""
+    c = cases["c1"]
+    shape = tuple(c["shape"])
+    ocase = oracle_case(c, shape)
+    rho = initial_rho(c, shape)
+    gpu = gpu_lattice(c, shape, FP64)
+    gpu.init(rho)
+    m0 = gpu.mass()
+    gpu.step(c["steps"])
+    f = oracle.step(ocase, oracle.equilibrium(ocase, rho), c["steps"])
+    ro = oracle.fields(ocase, f).rho
+    rg = gpu.fields()["rho"]
+    err = float(np.max(np.abs(rg - ro) / ro))
+    print("slab fp64 2000 steps: max rel err %.3e" % err)
+    assert err < 1e-10
+    assert np.allclose(gpu.mass(), m0, rtol=1e-12, atol=0)
+    assert np.allclose(oracle.mass(f), m0, rtol=1e-12, atol=0)
+
+
+def test_droplet_mrt_fp32_full_size(cases):
+    """The 3-component D2Q9 MRT FP32-shifted droplet at its full 512 x 512 size, 40 steps,
+    every site against the oracle."""
+    c = cases["c2"]
+    shape = tuple(c["shape"])
+    ocase = oracle_case(c, shape)
+    rho = initial_rho(c, shape)
+    gpu = gpu_lattice(c, shape, FP32S)
+    gpu.init(rho)
+    gpu.step(40)
+    f = oracle.step(ocase, oracle.equilibrium(ocase, rho), 40)
+    ro = oracle.fields(ocase, f).rho
+    rg = gpu.fields()["rho"]
+    err = float(np.max(np.abs(rg - ro) / ro))
+    print("droplet fp32s 40 steps: max rel err %.3e" % err)
+    assert err < 2e-4
+
+
+def _window(field, center, half):
+    """Periodic sub-box of a (..., nz, ny, nx) field around center (z, y, x)."""
+    out = field
+    for ax, (cc, n) in enumerate(zip(center, field.shape[-3:])):
+        idx = np.arange(cc - half, cc + half) % n
+        out = np.take(out, idx, axis=field.ndim - 3 + ax)
+    return out
+
+
+def test_sphere_d3q19_full_size_sampled(cases):
+    """The 3-component D3Q19 MRT FP32-shifted sphere at its full 256^3 size in the launch
+    configuration the benchmark times. The oracle cannot step 16.7 M sites, so sampled sites are
+    checked: after k steps a site depends only on sites within 2k (one pseudo-potential stencil
+    and one streaming hop per step), so the oracle steps a periodic 16^3 box around each sample
+    and its centre must agree with the full-grid GPU result."""
+    c = cases["c3"]
+    shape = tuple(c["shape"])
+    rho = initial_rho(c, shape)
+    gpu = gpu_lattice(c, shape, FP32S)
+    gpu.init(rho)
+    m0 = gpu.mass()
+    k = 3
+    gpu.step(k)
+    rg = gpu.fields(u=False, p=False, psi=False)["rho"]
+    n = shape[0]
+    r = 48.0
+    samples = [(0, 0, 0), (n // 2, n // 2, n // 2), (n // 2, n // 2, n // 2 + int(r)),
+               (n // 2 + 34, n // 2 - 34, n // 2 + 1), (n - 1, 5, n // 2 + int(r) - 1),
+               (n // 2 - int(r), n // 2, n // 2), (17, 200, 255), (n // 2, n // 2 + 28, n // 2 + 39)]
+    half = 8
+    ocase = oracle_case(c, (2 * half,) * 3)
+    worst = 0.0
+    for zc, yc, xc in samples:
+        sub = _window(rho, (zc, yc, xc), half)
+        f = oracle.step(ocase, oracle.equilibrium(ocase, np.ascontiguousarray(sub)), k)
+        ro = oracle.fields(ocase, f).rho[:, half, half, half]
+        got = rg[:, zc, yc, xc]
+        worst = max(worst, float(np.max(np.abs(got - ro) / ro)))
+    print("sphere fp32s sampled max rel err %.3e" % worst)
+    assert worst < 2e-4
+    gpu.step(97)
+    m1 = gpu.mass()
+    assert np.all(np.abs(m1 / m0 - 1) < 1e-5)
+
+
+def test_save_restore_is_bit_exact(cases):
+    c = cases["c2"]
+    shape = (64, 48)
+    rho = initial_rho(dict(c, init=dict(kind="ball", radius=12.0, width=4.0)), shape)
+    for prec in (FP64, FP32S):
+        gpu = gpu_lattice(c, shape, prec)
+        gpu.init(rho)
+        gpu.step(7)
+        buf, t = gpu.save()
+        gpu.step(13)
+        a = gpu.get_f()
+        gpu.restore(buf, t)
+        assert gpu.time == 7
+        gpu.step(13)
+        assert np.array_equal(gpu.get_f(), a)
+        # canonical round trip
+        f = gpu.get_f()
+        gpu.set_f(f)
+        assert np.array_equal(gpu.get_f(), f)
+        gpu.close()
+
+
+def test_domain_error_stops_before_collision(cases):
+    """G > 0 makes psi^2 negative: the first step reports LBM_ERR_PSI_DOMAIN, the populations
+    keep the state before it and the step counter stays at 0."""
+    from paper_1909_12390_gb300 import lbm
+    c = cases["c1"]
+    shape = (16, 16)
+    gpu = gpu_lattice(c, shape, FP64, G=1.0)
+    gpu.init(initial_rho(dict(c, init=dict(c["init"], lo=3.5, hi=11.5)), shape))
+    f0 = gpu.get_f()
+    with pytest.raises(lbm.LBMError) as ei:
+        gpu.step(5)
+    assert ei.value.status == lbm.ERR_PSI_DOMAIN
+    assert gpu.time == 0
+    assert np.array_equal(gpu.get_f(), f0)
+
+
+def test_nonfinite_state_is_reported(cases):
+    """A NaN planted in the raw storage on the host (lbm_restore does not validate) is caught by
+    the next step as LBM_ERR_NONFINITE."""
+    from paper_1909_12390_gb300 import lbm
+    c = cases["c1"]
+    shape = (16, 16)
+    gpu = gpu_lattice(c, shape, FP64)
+    gpu.init(initial_rho(dict(c, init=dict(c["init"], lo=3.5, hi=11.5)), shape))
+    gpu.step(4)
+    buf, t = gpu.save()
+    raw = buf.view(np.float64).copy()
+    raw[1234] = np.nan
+    gpu.restore(raw.view(np.uint8), t)
+    with pytest.raises(lbm.LBMError) as ei:
+        gpu.step(3)
+    assert ei.value.status == lbm.ERR_NONFINITE
+    assert gpu.time == 4
+
+
+@pytest.mark.parametrize("key", ["c2", "c3"])
+def test_full_length_runs_conserve_mass(cases, key):
+    """The FP32-shifted MRT droplet (20000 steps) and sphere (5000 steps) at full size and full
+    step count: no EOS-domain or non-finite step, per-component mass kept to FP32 rounding,
+    and the droplet still centred (the centre site stays liquid, a corner stays vapour)."""
+    c = cases[key]
+    shape = tuple(c["shape"])
+    rho = initial_rho(c, shape)
+    gpu = gpu_lattice(c, shape, FP32S)
+    gpu.init(rho)
+    m0 = rho.reshape(len(c["rho_l"]), -1).sum(1)
+    gpu.step(c["steps"])
+    assert gpu.time == c["steps"]
+    m1 = gpu.mass()
+    drift = np.abs(m1 / m0 - 1)
+    print(key, "mass drift", drift)
+    assert np.all(drift < 1e-4)
+    r = gpu.fields(u=False, p=False, psi=False)["rho"].sum(0)
+    centre = tuple(s // 2 for s in r.shape)
+    assert r[centre] > 0.5 * sum(c["rho_l"])
+    assert r[(0,) * r.ndim] < 2.0 * sum(c["rho_v"])
+    gpu.close()
