@@ -261,8 +261,10 @@ def main():
         stop.record(stream)
         torch.cuda.synchronize()
     ms_total = start.elapsed_time(stop)
+    path = gpu.path
     psi_ms, psi_n = gpu.profile_read(0)
     col_ms, col_n = gpu.profile_read(1)
+    fus_ms, fus_n = gpu.profile_read(2)
     gpu.profile(False)
     mass_end = gpu.mass()
     t_max = ms_total
@@ -273,20 +275,23 @@ def main():
     ms_step = t_max / args.steps
     value = N * nc * args.steps * world / (t_max / 1e3) / 1e6
 
-    # roofline of the dominant kernel (force + collide + in-place stream): algorithmic bytes
-    # are one read and one write of every FP32 population, 2 * 19 * nc * 4 B per site.
+    # roofline of the dominant kernel: algorithmic bytes are one read and one write of every
+    # FP32 population, 2 * 19 * nc * 4 B per site (the fused kernel and the collide pass each
+    # move exactly that; psi traffic is not counted)
     peak, peak_kind = peaks()
     alg_site = 2 * 19 * nc * 4
-    col_avg = col_ms / max(col_n, 1)
-    psi_avg = psi_ms / max(psi_n, 1)
-    dominant = "k_collide" if col_avg >= psi_avg else "k_psi"
-    achieved = N * alg_site / (col_avg / 1e3) / 1e9
+    if path == lbm.PATH_FUSED:
+        kname, kavg, kinds = "k_fused", fus_ms / max(fus_n, 1), {"k_fused": fus_ms / max(fus_n, 1)}
+    else:
+        kname, kavg = "k_collide", col_ms / max(col_n, 1)
+        kinds = {"k_psi": psi_ms / max(psi_n, 1), "k_collide": kavg}
+    achieved = N * alg_site / (kavg / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": ncu_traffic("k_collide"),
-            "kernel": "k_collide<19,3,FP32S,MRT>", "peak_kind": peak_kind,
+            "frac": achieved / peak, "traffic": ncu_traffic(kname),
+            "kernel": "%s<19,%d,FP32S,MRT>" % (kname, nc), "peak_kind": peak_kind,
             "alg_bytes_per_launch": N * alg_site,
             "step_frac": (N * alg_site / (ms_step / 1e3) / 1e9) / peak,
-            "kernels_ms_avg": {"k_psi": psi_avg, "k_collide": col_avg}, "dominant": dominant}
+            "kernels_ms_avg": kinds, "path": "fused" if path == lbm.PATH_FUSED else "two-kernel"}
 
     # end to end through the C ABI with host buffers
     gpu.set_stream(0)
@@ -322,7 +327,21 @@ def main():
         g64.close()
         variants["fp64"] = {"value": N * nc / (ms64 / 1e3) / 1e6, "ms_per_step": ms64,
                             "hbm_frac_of_step": (N * 2 * 19 * nc * 8 / (ms64 / 1e3) / 1e9) / peak}
-        variants["fp32s"] = {"value": value, "ms_per_step": ms_step}
+        variants["fp32s"] = {"value": value, "ms_per_step": ms_step, "path": roof["path"]}
+        # the same workload on the two-kernel path
+        g2 = lattice_for(c, lbm.FP32_SHIFTED)
+        g2.set_path(lbm.PATH_TWO_KERNEL)
+        g2.init(rho0)
+        g2.step(3)
+        g2.set_stream(stream.cuda_stream)
+        a.record(stream)
+        g2.step(50)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms2 = a.elapsed_time(b) / 50
+        g2.close()
+        variants["fp32s_two_kernel"] = {"value": N * nc / (ms2 / 1e3) / 1e6, "ms_per_step": ms2,
+                                        "hbm_frac_of_step": (N * alg_site / (ms2 / 1e3) / 1e9) / peak}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -330,7 +349,7 @@ def main():
            "config": {"workload": WORKLOAD, "lattice": "D3Q19", "grid": c["shape"], "components": nc,
                       "collision": "mrt", "precision": "fp32-shifted", "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs larger than L2 (%.2f GB populations)" % (N * 19 * nc * 4 / 1e9)},
-           "e2e": e2e, "roofline": roof, "gpu_launches": psi_n + col_n,
+           "e2e": e2e, "roofline": roof, "gpu_launches": psi_n + col_n + fus_n,
            "clocks": clk.summary(), "site_mlups": value / nc,
            "mass_drift": float(np.max(np.abs(mass_end / (rho0.reshape(nc, -1).sum(1)) - 1)))}
     if variants:

@@ -141,11 +141,33 @@ size_t lbm_state_bytes(const lbm_ctx *ctx);
 lbm_status lbm_save(lbm_ctx *ctx, void *buf, size_t bytes, int64_t *t);
 lbm_status lbm_restore(lbm_ctx *ctx, const void *buf, size_t bytes, int64_t t);
 
+/* Step path. LBM_PATH_FUSED runs one persistent cooperative kernel per step: each block
+ * marches a tile column (32 x 8 sites for D3Q19 along z, 128 sites for D2Q9 along y), computes
+ * psi once per site, publishes it plane by plane and collides a plane once its neighbour tiles
+ * have published the planes around it (waits are bounded; LBM_ERR_TIMEOUT if one runs out,
+ * after which the state is undefined). It needs nx divisible by the tile width (and ny by 8
+ * for D3Q19) and all blocks co-resident. LBM_PATH_TWO_KERNEL runs a pseudo-potential pass and
+ * a collide-stream pass. LBM_PATH_AUTO (the default at lbm_create) takes the fused path when
+ * it fits. Setting LBM_PATH_FUSED on a grid it does not fit returns LBM_ERR_ARG and leaves the
+ * two-kernel path. Both paths compute the same arithmetic in the same order per site. */
+enum { LBM_PATH_AUTO = 0, LBM_PATH_TWO_KERNEL = 1, LBM_PATH_FUSED = 2 };
+lbm_status lbm_set_path(lbm_ctx *ctx, int path);
+/* The path lbm_step takes now (LBM_PATH_TWO_KERNEL or LBM_PATH_FUSED). */
+int lbm_get_path(const lbm_ctx *ctx);
+
+/* Failure-detection test hook, fused path only: from the next step on, fused block `block`
+ * (0-based, x-tile fastest, then y-tile, then chunk) computes but never publishes its
+ * progress, so every neighbour's bounded wait runs out and lbm_step returns
+ * LBM_ERR_TIMEOUT (within about a second per step, without faulting or hanging the GPU); the
+ * populations are then undefined. -1 switches the hook off; lbm_init restores a state. */
+lbm_status lbm_test_silence_block(lbm_ctx *ctx, int block);
+
 /* Kernel timing. lbm_profile(ctx, 1) clears the record and from then on brackets every
  * kernel launch of lbm_step with CUDA events on the context's stream (graph replay is off
  * while profiling); lbm_profile(ctx, 0) stops recording. lbm_profile_read sums the recorded
  * durations of one kernel kind (0 = pseudo-potential pass, 1 = force + collide + stream
- * pass) in milliseconds and gives the number of launches. Both synchronise the stream. */
+ * pass, 2 = fused step) in milliseconds and gives the number of launches. Both synchronise
+ * the stream. */
 lbm_status lbm_profile(lbm_ctx *ctx, int on);
 lbm_status lbm_profile_read(lbm_ctx *ctx, int kernel, double *total_ms, int64_t *launches);
 

@@ -13,6 +13,7 @@
 
 #include "lbm.h"
 #include "lbm_core.cuh"
+#include "lbm_kernels.cuh"
 #include "lbm_ops.h"
 
 namespace lbm {
@@ -62,10 +63,15 @@ struct lbm_ctx {
   int64_t t = 0;
   cudaGraphExec_t graph = nullptr;
   bool graph_failed = false;
+  // step path: the fused kernel when its tiling fits the grid and its blocks are co-resident
+  int path_request = LBM_PATH_AUTO;
+  bool fused = false;
+  lbm::FusedArgs fargs{};
+  cudaError_t launch_err = cudaSuccess;
   // per-kernel event timing (lbm_profile): events recorded around every launch on the stream
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::pair<int, int>> ev_marks[2];  // (start, stop) pool indices per kernel kind
+  std::vector<std::pair<int, int>> ev_marks[3];  // (start, stop) pool indices per kernel kind
   size_t ev_used = 0;
   std::string err;
 };
@@ -143,6 +149,20 @@ void launch_steps(lbm_ctx* c, int64_t n, int64_t t0) {
   for (int64_t i = 0; i < n; ++i) {
     int parity = (int)((t0 + i) & 1);
     int e0 = -1, e1 = -1, e2 = -1;
+    if (c->fused) {
+      if (c->profiling) {
+        e0 = next_event(c);
+        e1 = next_event(c);
+      }
+      if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], c->stream);
+      cudaError_t e = c->ops->fused(c->P, c->f, c->psi, c->status, c->t_dev, c->fargs, c->stream);
+      if (e != cudaSuccess && c->launch_err == cudaSuccess) c->launch_err = e;
+      if (e1 >= 0) {
+        cudaEventRecord(c->ev_pool[e1], c->stream);
+        c->ev_marks[2].push_back({e0, e1});
+      }
+      continue;
+    }
     if (c->profiling) {
       e0 = next_event(c);
       e1 = next_event(c);
@@ -163,6 +183,60 @@ void launch_steps(lbm_ctx* c, int64_t n, int64_t t0) {
 void drop_graph(lbm_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   c->graph = nullptr;
+}
+
+void free_fused(lbm_ctx* c) {
+  cudaFree(c->fargs.flags);
+  cudaFree(c->fargs.done);
+  cudaFree(c->fargs.pending);
+  c->fargs = lbm::FusedArgs{};
+  c->fused = false;
+}
+
+// Chooses the fused tiling: tiles of fused_tx x fused_ty sites across the grid, the slowest
+// axis cut into the largest number of chunks (each >= 4 planes) whose blocks are still all
+// co-resident. Returns false when the grid does not tile or the blocks would not fit.
+bool setup_fused(lbm_ctx* c) {
+  free_fused(c);
+  const int TX = c->ops->fused_tx, TY = c->ops->fused_ty;
+  const bool d3 = c->Q == 19;
+  const int nx = c->P.nx, ny = c->P.ny, nz = c->P.nz;
+  const int nm = d3 ? nz : ny;
+  if (nx % TX != 0 || (d3 && ny % TY != 0)) return false;
+  const int ntx = nx / TX, nty = d3 ? ny / TY : 1;
+  const int cap = c->ops->fused_max_blocks();
+  const long long tiles = (long long)ntx * nty;
+  int best = 0;
+  for (int nch = 1; nch <= nm; ++nch)
+    if (nm % nch == 0 && nm / nch >= 4 && tiles * nch <= cap) best = nch;
+  if (best == 0) return false;
+  const size_t nb = (size_t)tiles * best;
+  lbm::FusedArgs a{};
+  a.ntx = ntx;
+  a.nty = nty;
+  a.nchunk = best;
+  a.L = nm / best;
+  a.silent_block = -1;
+  if (cudaMalloc(&a.flags, nb * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&a.done, sizeof(unsigned int)) != cudaSuccess || cudaMalloc(&a.pending, sizeof(int)) != cudaSuccess ||
+      cudaMemset(a.flags, 0, nb * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(a.done, 0, sizeof(unsigned int)) != cudaSuccess || cudaMemset(a.pending, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    c->fargs = a;
+    free_fused(c);
+    return false;
+  }
+  c->fargs = a;
+  c->fused = true;
+  return true;
+}
+
+// Progress counters must not exceed t * L when the step counter is reset or rewound.
+cudaError_t reset_fused_flags(lbm_ctx* c) {
+  if (!c->fused) return cudaSuccess;
+  return cudaMemsetAsync(c->fargs.flags, 0,
+                         (size_t)c->fargs.ntx * c->fargs.nty * c->fargs.nchunk * sizeof(unsigned long long),
+                         c->stream);
 }
 
 // Captures kGraphSteps steps starting at an even step; on any capture failure the context
@@ -241,8 +315,9 @@ lbm_status lbm_create(const lbm_grid* grid, int nc, const lbm_component* comps, 
     for (int k = 0; k < Q; ++k)
       if (!std::isfinite(eos->mrt_rates[k]) || !(eos->mrt_rates[k] > 0) || !(eos->mrt_rates[k] < 2))
         return fail(nullptr, LBM_ERR_ARG, "mrt_rates[%d] must lie in (0, 2)", k);
-  const lbm::Ops* ops = Q == 9 ? lbm::ops_q9(nc, eos->precision, eos->collision)
-                               : lbm::ops_q19(nc, eos->precision, eos->collision);
+  const bool f64 = eos->precision == LBM_FP64;
+  const lbm::Ops* ops = Q == 9 ? (f64 ? lbm::ops_q9_f64 : lbm::ops_q9_f32s)(nc, eos->collision)
+                               : (f64 ? lbm::ops_q19_f64 : lbm::ops_q19_f32s)(nc, eos->collision);
   if (!ops) return fail(nullptr, LBM_ERR_ARG, "no kernels for this configuration");
 
   lbm_ctx* c = new (std::nothrow) lbm_ctx();
@@ -275,9 +350,16 @@ lbm_status lbm_create(const lbm_grid* grid, int nc, const lbm_component* comps, 
     P.gamma[i] = eos->gamma ? eos->gamma[i] : 1.0;
     P.rho_ref[i] = (eos->precision == LBM_FP32_SHIFTED && eos->rho_ref) ? eos->rho_ref[i] : 0.0;
   }
-  for (int i = 0; i < nc; ++i)
-    for (int j = 0; j < nc; ++j)
-      P.Qa[i * 4 + j] = std::sqrt(aa[i] * aa[j]) * (1.0 - (eos->kij ? eos->kij[i * nc + j] : 0.0));
+  P.kij_zero = 1;
+  for (int i = 0; i < nc; ++i) {
+    P.sa[i] = std::sqrt(aa[i]);
+    P.invMf[i] = (float)(1.0 / comps[i].M);
+    for (int j = 0; j < nc; ++j) {
+      const double k = eos->kij ? eos->kij[i * nc + j] : 0.0;
+      if (k != 0.0) P.kij_zero = 0;
+      P.Qa[i * 4 + j] = std::sqrt(aa[i] * aa[j]) * (1.0 - k);
+    }
+  }
   P.RT = R * eos->T;
   P.cpsi = 2.0 / (eos->G * (1.0 / 3.0));
   P.beta = eos->beta;
@@ -299,6 +381,7 @@ lbm_status lbm_create(const lbm_grid* grid, int nc, const lbm_component* comps, 
     return st;
   }
   c->stream = c->own;
+  setup_fused(c);
   *out = c;
   return LBM_OK;
 }
@@ -307,6 +390,7 @@ void lbm_destroy(lbm_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_graph(c);
+  free_fused(c);
   cudaFree(c->f);
   cudaFree(c->psi);
   cudaFree(c->status);
@@ -326,11 +410,12 @@ lbm_status lbm_profile(lbm_ctx* c, int on) {
   c->ev_used = 0;
   c->ev_marks[0].clear();
   c->ev_marks[1].clear();
+  c->ev_marks[2].clear();
   return LBM_OK;
 }
 
 lbm_status lbm_profile_read(lbm_ctx* c, int kernel, double* total_ms, int64_t* launches) {
-  if (!c || kernel < 0 || kernel > 1) return c ? fail(c, LBM_ERR_ARG, "kernel must be 0 or 1") : LBM_ERR_ARG;
+  if (!c || kernel < 0 || kernel > 2) return c ? fail(c, LBM_ERR_ARG, "kernel must be 0, 1 or 2") : LBM_ERR_ARG;
   CK(c, cudaStreamSynchronize(c->stream));
   double sum = 0;
   for (auto& m : c->ev_marks[kernel]) {
@@ -382,6 +467,7 @@ lbm_status lbm_init(lbm_ctx* c, const double* rho, const double* u) {
   CK(c, cudaGetLastError());
   CK(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
   CK(c, cudaMemsetAsync(c->t_dev, 0, sizeof(long long), c->stream));
+  CK(c, reset_fused_flags(c));
   CK(c, cudaStreamSynchronize(c->stream));
   c->t = 0;
   return LBM_OK;
@@ -402,9 +488,46 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n) {
     left -= kGraphSteps;
   }
   launch_steps(c, left, t);
+  if (c->launch_err != cudaSuccess) {
+    cudaError_t e = c->launch_err;
+    c->launch_err = cudaSuccess;
+    cudaStreamSynchronize(c->stream);
+    return cuda_fail(c, e, "fused step launch");
+  }
   CK(c, cudaGetLastError());
   return sync_status(c);
 }
+
+lbm_status lbm_set_path(lbm_ctx* c, int path) {
+  if (!c) return LBM_ERR_ARG;
+  if (path != LBM_PATH_AUTO && path != LBM_PATH_TWO_KERNEL && path != LBM_PATH_FUSED)
+    return fail(c, LBM_ERR_ARG, "unknown path %d", path);
+  CK(c, cudaStreamSynchronize(c->stream));
+  drop_graph(c);
+  c->graph_failed = false;
+  c->path_request = path;
+  if (path == LBM_PATH_TWO_KERNEL) {
+    free_fused(c);
+    return LBM_OK;
+  }
+  if (!setup_fused(c) && path == LBM_PATH_FUSED)
+    return fail(c, LBM_ERR_ARG, "the fused step does not fit this grid (tiles %dx%d, co-residency)",
+                c->ops->fused_tx, c->ops->fused_ty);
+  return LBM_OK;
+}
+
+lbm_status lbm_test_silence_block(lbm_ctx* c, int block) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->fused) return fail(c, LBM_ERR_ARG, "the fused path is not active");
+  const int nb = c->fargs.ntx * c->fargs.nty * c->fargs.nchunk;
+  if (block < -1 || block >= nb) return fail(c, LBM_ERR_ARG, "block must be -1 or in [0, %d)", nb);
+  CK(c, cudaStreamSynchronize(c->stream));
+  drop_graph(c);
+  c->fargs.silent_block = block;
+  return LBM_OK;
+}
+
+int lbm_get_path(const lbm_ctx* c) { return c ? (c->fused ? LBM_PATH_FUSED : LBM_PATH_TWO_KERNEL) : -1; }
 
 int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
 
@@ -471,6 +594,7 @@ lbm_status lbm_set_f(lbm_ctx* c, const double* f) {
   cudaFreeAsync(d, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->t_dev, 0, sizeof(long long), c->stream);
+  if (e == cudaSuccess) e = reset_fused_flags(c);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "lbm_set_f");
   c->t = 0;
@@ -498,6 +622,7 @@ lbm_status lbm_restore(lbm_ctx* c, const void* buf, size_t bytes, int64_t t) {
   long long tt = t;
   CK(c, cudaMemcpyAsync(c->t_dev, &tt, sizeof(long long), cudaMemcpyHostToDevice, c->stream));
   CK(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+  CK(c, reset_fused_flags(c));
   CK(c, cudaStreamSynchronize(c->stream));
   c->t = t;
   return LBM_OK;

@@ -118,6 +118,9 @@ struct Params {
   double invM[4];    // 1 / M_i
   double b[4];       // b_i (molar co-volume)
   double Qa[16];     // sqrt(a_i alpha_i a_j alpha_j) (1 - zeta_ij)
+  double sa[4];      // sqrt(a_i alpha_i)
+  int kij_zero;      // every zeta_ij == 0: [a alpha]_m n^2 = (sum_i n_i sa_i)^2
+  float invMf[4];    // 1 / M_i in FP32
   double RT;
   double cpsi;       // 2 / (G cs2): psi^2 = cpsi (p - cs2 rho)
   double rho_ref[4]; // FP32 shift references (0 for FP64 storage)
@@ -221,6 +224,45 @@ __device__ __forceinline__ EosOut<NC> eos_pr(const Params& P, const double (&rho
 #pragma unroll
     for (int j = i + 1; j < NC; ++j) v = fma(2.0 * P.Qa[i * 4 + j], n[j], v);
     A2 = fma(n[i], v, A2);
+  }
+  double d1 = 1.0 - B;
+  double d2 = fma(B, 2.0 - B, 1.0);
+  EosOut<NC> o;
+  o.Dd = d1 * d2;
+  o.pD = fma(nt * P.RT, d2, -A2 * d1);
+  o.B = B;
+  return o;
+}
+
+// The same pressure from FP32 cell-volume densities (FP32-shifted storage): the molar
+// densities n_i = rho_i / M_i are formed in FP32 (their inputs carry FP32 precision), every
+// sum of the EOS and the numerator with its cancellation run in FP64. With all zeta_ij = 0
+// the mixing rule collapses to A2 = (sum_i n_i sqrt(a_i alpha_i))^2.
+template <int NC>
+__device__ __forceinline__ EosOut<NC> eos_pr_f32in(const Params& P, const float (&rho)[NC]) {
+  double n[NC];
+  double nt = 0.0, B = 0.0;
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    n[i] = (double)(rho[i] * P.invMf[i]);
+    nt += n[i];
+    B = fma(P.b[i], n[i], B);
+  }
+  double A2;
+  if (P.kij_zero) {
+    double S = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; ++i) S = fma(P.sa[i], n[i], S);
+    A2 = S * S;
+  } else {
+    A2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      double v = P.Qa[i * 4 + i] * n[i];
+#pragma unroll
+      for (int j = i + 1; j < NC; ++j) v = fma(2.0 * P.Qa[i * 4 + j], n[j], v);
+      A2 = fma(n[i], v, A2);
+    }
   }
   double d1 = 1.0 - B;
   double d2 = fma(B, 2.0 - B, 1.0);

@@ -1,7 +1,13 @@
-// Kernels of the two-kernel step (pseudo-potential pass, then force + collide + in-place
-// stream) and of the context's set-up and read-back, templated on the lattice, the number of
-// components and the storage precision. Included once per lattice by lbm_d2q9.cu and
-// lbm_d3q19.cu, which instantiate the dispatch tables.
+// Kernels of one time step, templated on the lattice, the number of components and the
+// storage precision, and the context's set-up / read-back kernels. lbm_<lattice>_<storage>.cu
+// instantiate the dispatch tables, one translation unit per lattice and storage type.
+//
+// Two step paths share the per-site bodies site_psi (S1-S3) and site_collide (S4-S6):
+//   * two-kernel: k_psi over every site, then k_collide over every site;
+//   * fused: k_fused, one persistent cooperative launch per step in which every block marches
+//     its tile column along the slowest axis, computes psi once per site, publishes each plane
+//     of psi with a release flag, waits (bounded) for its neighbour tiles' flags and then
+//     collides and streams the plane in place.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -24,109 +30,96 @@ struct PrecF32S {
 
 constexpr int kBlock = 256;
 
-__device__ __forceinline__ void raise_status(int* status, int bit) { atomicOr(status, bit); }
-
 // ---------------------------------------------------------------------------------------
-// Pass 1: cell-volume densities (S1), EOS (S2) and pseudo-potential (S3) of every site.
+// S1-S3 of one site: cell-volume densities, mixture Peng-Robinson EOS, pseudo-potential.
+// Returns 0 or status bits; psi_out is 0 on error.
 template <int Q, int NC, class Prec>
-__global__ void __launch_bounds__(kBlock) k_psi(const Params P, const typename Prec::S* __restrict__ f,
-                                                typename Prec::PsiT* __restrict__ psi, int* status,
-                                                int parity) {
+__device__ __forceinline__ int site_psi(const Params& P, const typename Prec::S* __restrict__ f, const Site& s,
+                                        int64_t idx, int parity, typename Prec::PsiT& psi_out) {
   using R = typename Prec::R;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= P.N) return;
-  if (*(volatile int*)status) return;
-  Site s;
-  s.set(P, idx);
   R d[NC];
   For<0, NC>::run([&]<int C>() {
     R acc = 0;
     For<0, Q>::run([&]<int A>() { acc += (R)f[AA<Q>::template read_slot<A>(P, s, idx, parity, C)]; });
     d[C] = acc;
   });
-  double rho[NC];
   R rho_t = 0;
+  double pD, Dd, B;
+  if constexpr (sizeof(R) == 8) {
+    double rho[NC];
 #pragma unroll
-  for (int i = 0; i < NC; ++i) {
-    rho[i] = P.rho_ref[i] + (double)d[i];
-    rho_t += (R)P.rho_ref[i] + d[i];
+    for (int i = 0; i < NC; ++i) {
+      rho[i] = P.rho_ref[i] + d[i];
+      rho_t += rho[i];
+    }
+    EosOut<NC> e = eos_pr<NC>(P, rho);
+    pD = e.pD; Dd = e.Dd; B = e.B;
+  } else {
+    float rc[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      rc[i] = (float)P.rho_ref[i] + d[i];
+      rho_t += rc[i];
+    }
+    EosOut<NC> e = eos_pr_f32in<NC>(P, rc);
+    pD = e.pD; Dd = e.Dd; B = e.B;
   }
-  EosOut<NC> e = eos_pr<NC>(P, rho);
   R psi2;
   if constexpr (sizeof(R) == 8) {
-    psi2 = P.cpsi * (e.pD / e.Dd - rho_t * (1.0 / 3.0));
+    psi2 = P.cpsi * (pD / Dd - rho_t * (1.0 / 3.0));
   } else {
     // the quotient and everything after it are well conditioned: FP32, like the stored psi
-    psi2 = (float)P.cpsi * ((float)e.pD / (float)e.Dd - rho_t * (1.0f / 3.0f));
+    psi2 = (float)P.cpsi * ((float)pD / (float)Dd - rho_t * (1.0f / 3.0f));
   }
-  if (!isfinite(psi2) || !isfinite(rho_t)) {
-    raise_status(status, ST_NONFINITE);
-    return;
-  }
-  if (!(e.B < 1.0) || psi2 < (R)0) {
-    raise_status(status, ST_PSI_DOMAIN);
-    return;
-  }
-  psi[idx] = (typename Prec::PsiT)sqrt(psi2);
+  psi_out = 0;
+  if (!isfinite(psi2) || !isfinite(rho_t)) return ST_NONFINITE;
+  if (!(B < 1.0) || psi2 < (R)0) return ST_PSI_DOMAIN;
+  psi_out = (typename Prec::PsiT)sqrt(psi2);
+  return 0;
 }
 
-// ---------------------------------------------------------------------------------------
-// Pass 2: total force (S4), split (S5), Guo-forced BGK or MRT collision and in-place AA
-// streaming (S6).
+// S4-S6 of one site given psi at the site (pn[0]) and its Q - 1 neighbours (pn[a] at x + e_a):
+// total force, split, Guo-forced BGK or MRT collision, in-place AA write.
 template <int Q, int NC, class Prec, int MRT>
-__global__ void __launch_bounds__(kBlock) k_collide(const Params P, typename Prec::S* __restrict__ f,
-                                                    const typename Prec::PsiT* __restrict__ psi,
-                                                    const int* status, long long* t_dev, int parity) {
+__device__ __forceinline__ void site_collide(const Params& P, typename Prec::S* __restrict__ f, const Site& s,
+                                             int64_t idx, int parity, const typename Prec::R (&pn)[Q]) {
   using R = typename Prec::R;
   using L = Lat<Q>;
   constexpr int D = L::D;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= P.N) return;
-  if (*(volatile const int*)status) return;
-  // the step counter advances only for steps whose pseudo-potential pass succeeded
-  if (idx == 0) *t_dev += 1;
-  Site s;
-  s.set(P, idx);
-
-  R fl[NC][Q];
-  For<0, NC>::run([&]<int C>() {
-    For<0, Q>::run([&]<int A>() { fl[C][A] = (R)f[AA<Q>::template read_slot<A>(P, s, idx, parity, C)]; });
-  });
 
   // S4: F = -beta G psi(x) sum_a w_a psi(x+e_a) e_a - (1-beta)/2 G sum_a w_a psi^2(x+e_a) e_a
   R s1[3] = {0, 0, 0}, s2[3] = {0, 0, 0};
-  For<1, Q>::run([&]<int A>() {
-    R pn = (R)psi[s.nb(P, L::e(A, 0), L::e(A, 1), L::e(A, 2))];
-    R wp = (R)L::w(A) * pn;
-    R wq = wp * pn;
+#pragma unroll
+  for (int a = 1; a < Q; ++a) {
+    R wp = (R)L::w(a) * pn[a];
+    R wq = wp * pn[a];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      if (L::e(A, d) > 0) { s1[d] += wp; s2[d] += wq; }
-      if (L::e(A, d) < 0) { s1[d] -= wp; s2[d] -= wq; }
+      if (L::e(a, d) > 0) { s1[d] += wp; s2[d] += wq; }
+      if (L::e(a, d) < 0) { s1[d] -= wp; s2[d] -= wq; }
     }
-  });
-  const R p0 = (R)psi[idx];
+  }
   const R c1 = (R)(-P.beta * P.G), c2 = (R)(-0.5 * (1.0 - P.beta) * P.G);
   R F[3] = {0, 0, 0};
 #pragma unroll
-  for (int d = 0; d < D; ++d) F[d] = c1 * p0 * s1[d] + c2 * s2[d];
+  for (int d = 0; d < D; ++d) F[d] = c1 * pn[0] * s1[d] + c2 * s2[d];
 
-  // S1 moments: shifted densities delta_c = rho_c - rho_ref_c and total momentum j
+  // S1 moments, first pass over the populations: shifted densities delta_c = rho_c - rho_ref_c
+  // and total momentum j. The second pass (per component, below) reloads them from L1.
   R dl[NC], j[3] = {0, 0, 0};
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
+  For<0, NC>::run([&]<int C>() {
     R acc = 0;
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-      acc += fl[c][a];
+    For<0, Q>::run([&]<int A>() {
+      const R v = (R)f[AA<Q>::template read_slot<A>(P, s, idx, parity, C)];
+      acc += v;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        if (L::e(a, d) > 0) j[d] += fl[c][a];
-        if (L::e(a, d) < 0) j[d] -= fl[c][a];
+        if (L::e(A, d) > 0) j[d] += v;
+        if (L::e(A, d) < 0) j[d] -= v;
       }
-    }
-    dl[c] = acc;
-  }
+    });
+    dl[C] = acc;
+  });
   R rc[NC], rho = 0, gs = 0;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
@@ -139,16 +132,16 @@ __global__ void __launch_bounds__(kBlock) k_collide(const Params P, typename Pre
   const R irho = (R)1 / rho;
 #pragma unroll
   for (int d = 0; d < D; ++d) u[d] = (j[d] + (R)0.5 * F[d]) * irho;
-  R uu = 0;
+  R uu = 0, uF = 0;
 #pragma unroll
-  for (int d = 0; d < D; ++d) uu += u[d] * u[d];
+  for (int d = 0; d < D; ++d) {
+    uu += u[d] * u[d];
+    uF += u[d] * F[d];
+  }
 
   // per-site equilibrium polynomial P_a = 3 e.u + 9/2 (e.u)^2 - 3/2 u.u and the Guo term of the
   // total force Fb_a = w_a [3 (e_a - u).F + 9 (e_a.u)(e_a.F)]; component s uses chi_s Fb_a.
   R Pa[Q], Fb[Q];
-  R uF = 0;
-#pragma unroll
-  for (int d = 0; d < D; ++d) uF += u[d] * F[d];
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
     R eu = 0, eF = 0;
@@ -167,12 +160,12 @@ __global__ void __launch_bounds__(kBlock) k_collide(const Params P, typename Pre
   For<0, NC>::run([&]<int C>() {
     const R chi = (R)P.gamma[C] * rc[C] * igs;  // S5
     R g[Q], out[Q];
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
+    For<0, Q>::run([&]<int A>() {
+      const R v = (R)f[AA<Q>::template read_slot<A>(P, s, idx, parity, C)];
       // non-equilibrium part: f - f_eq in the stored (shifted) variables
-      g[a] = fl[C][a] - (R)L::w(a) * (dl[C] + rc[C] * Pa[a]);
-      out[a] = fl[C][a] - om * g[a] + gk * chi * Fb[a];
-    }
+      g[A] = v - (R)L::w(A) * (dl[C] + rc[C] * Pa[A]);
+      out[A] = v - om * g[A] + gk * chi * Fb[A];
+    });
     if constexpr (MRT) {
       // rows with their own rate: f* -= sum_k M_ka lam_k (M q)_k, q = g + chi Fb / 2
       R q[Q];
@@ -197,6 +190,226 @@ __global__ void __launch_bounds__(kBlock) k_collide(const Params P, typename Pre
       f[AA<Q>::template write_slot<A>(P, s, idx, parity, C)] = (typename Prec::S)out[A];
     });
   });
+}
+
+// ---------------------------------------------------------------------------------------
+// Two-kernel step.
+
+// Pass 1: S1-S3 of every site.
+template <int Q, int NC, class Prec>
+__global__ void __launch_bounds__(kBlock) k_psi(const Params P, const typename Prec::S* __restrict__ f,
+                                                typename Prec::PsiT* __restrict__ psi, int* status,
+                                                int parity) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P.N) return;
+  if (*(volatile int*)status) return;
+  Site s;
+  s.set(P, idx);
+  typename Prec::PsiT v;
+  int e = site_psi<Q, NC, Prec>(P, f, s, idx, parity, v);
+  if (e) {
+    atomicOr(status, e);
+    return;
+  }
+  psi[idx] = v;
+}
+
+// Pass 2: S4-S6 of every site; psi of the neighbours from global memory.
+template <int Q, int NC, class Prec, int MRT>
+__global__ void __launch_bounds__(kBlock, 2) k_collide(const Params P, typename Prec::S* __restrict__ f,
+                                                    const typename Prec::PsiT* __restrict__ psi,
+                                                    const int* status, long long* t_dev, int parity) {
+  using R = typename Prec::R;
+  using L = Lat<Q>;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P.N) return;
+  if (*(volatile const int*)status) return;
+  // the step counter advances only for steps whose pseudo-potential pass succeeded
+  if (idx == 0) *t_dev += 1;
+  Site s;
+  s.set(P, idx);
+  R pn[Q];
+  pn[0] = (R)psi[idx];
+#pragma unroll
+  for (int a = 1; a < Q; ++a) pn[a] = (R)psi[s.nb(P, L::e(a, 0), L::e(a, 1), L::e(a, 2))];
+  site_collide<Q, NC, Prec, MRT>(P, f, s, idx, parity, pn);
+}
+
+// ---------------------------------------------------------------------------------------
+// Fused step.
+template <int Q>
+struct Fused;
+template <>
+struct Fused<19> {  // tile of 32 x 8 sites in (x, y), march along z
+  static constexpr int TX = 32, TY = 8, NT = TX * TY, WY = TY + 2;
+};
+template <>
+struct Fused<9> {  // tile of 128 sites in x, march along y
+  static constexpr int TX = 128, TY = 1, NT = TX, WY = 1;
+};
+
+struct FusedArgs {
+  unsigned long long* flags;  // one progress counter per block (stages published)
+  unsigned int* done;         // blocks finished in the current launch
+  int* pending;               // status bits raised in the current launch
+  int ntx, nty, nchunk, L;    // tiles along x and y (1 in 2-D), chunks and chunk length
+  int silent_block;           // test hook: this block publishes no progress (-1: none)
+};
+
+constexpr unsigned kSpinLimit = 1u << 20;  // polls of one flag before giving up (~1 s)
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <int Q, int NC, class Prec, int MRT>
+__global__ void __launch_bounds__(Fused<Q>::NT, Q == 19 ? 2 : 4)
+    k_fused(const Params P, typename Prec::S* __restrict__ f, typename Prec::PsiT* __restrict__ psi_g, int* status,
+            long long* t_dev, const FusedArgs A) {
+  using G = Fused<Q>;
+  using R = typename Prec::R;
+  using PsiT = typename Prec::PsiT;
+  using L = Lat<Q>;
+  constexpr bool D3 = Q == 19;
+  constexpr int TX = G::TX, TY = G::TY, WY = G::WY, WX = TX + 2;
+  __shared__ PsiT win[3][WY][WX];
+  __shared__ int nbr[27];
+  __shared__ int nbr_need[27];  // 0 = same chunk, 1 = chunk below, 2 = chunk above
+  __shared__ int n_nbr;
+
+  if (*(volatile int*)status) return;  // a previous step failed: do nothing
+  const unsigned long long t = (unsigned long long)*(volatile long long*)t_dev;
+  const int parity = (int)(t & 1);
+  const int L_ = A.L;
+  const unsigned long long base = t * (unsigned long long)L_;
+  const int b = blockIdx.x;
+  const int tx = b % A.ntx;
+  const int ty = (b / A.ntx) % A.nty;
+  const int ch = b / (A.ntx * A.nty);
+  const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
+  const int cx = tx * TX + lx;
+  const int cy = D3 ? ty * TY + ly : 0;
+  const int nm = D3 ? P.nz : P.ny;
+  const int p0 = ch * L_;
+
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int kind = 0; kind < 3; ++kind) {
+      int cc = kind == 0 ? ch : (kind == 1 ? (ch + A.nchunk - 1) % A.nchunk : (ch + 1) % A.nchunk);
+      for (int dy = D3 ? -1 : 0; dy <= (D3 ? 1 : 0); ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          if (kind == 0 && dx == 0 && dy == 0) continue;
+          int ttx = (tx + dx + A.ntx) % A.ntx, tty = (ty + dy + A.nty) % A.nty;
+          nbr[n] = (cc * A.nty + tty) * A.ntx + ttx;
+          nbr_need[n] = kind;
+          ++n;
+        }
+    }
+    n_nbr = n;
+  }
+
+  auto site_index = [&](int m) -> int64_t {
+    return D3 ? ((int64_t)m * P.ny + cy) * P.nx + cx : (int64_t)m * P.nx + cx;
+  };
+  int err = 0;
+  // stage s computes psi of plane p(s): s = 0 the chunk's last plane, s >= 1 plane p0 + s - 1
+  auto stage = [&](int s_) {
+    const int m = s_ == 0 ? p0 + L_ - 1 : p0 + s_ - 1;
+    const int64_t idx = site_index(m);
+    Site st;
+    st.set(P, idx);
+    PsiT v;
+    err |= site_psi<Q, NC, Prec>(P, f, st, idx, parity, v);
+    psi_g[idx] = v;
+    __syncthreads();
+    if (threadIdx.x == 0 && b != A.silent_block) st_release_u64(&A.flags[b], base + (unsigned long long)(s_ + 1));
+  };
+  bool ok = true;
+  // waits until every neighbour of the selected kind has published `need` stages
+  auto wait = [&](int kind, int need) {
+    bool mine = true;
+    if (ok && threadIdx.x < n_nbr && nbr_need[threadIdx.x] == kind) {
+      const unsigned long long target = base + (unsigned long long)need;
+      const unsigned long long* fl = &A.flags[nbr[threadIdx.x]];
+      unsigned it = 0;
+      while (ld_acquire_u64(fl) < target) {
+        if (++it > kSpinLimit) {
+          mine = false;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    ok = __syncthreads_and(mine && ok) != 0;
+  };
+  // psi window of plane m (periodic) into slot, through L2 (written by other blocks)
+  auto load_window = [&](int m, int slot) {
+    const int gm = (m % nm + nm) % nm;
+    for (int i = threadIdx.x; i < WY * WX; i += G::NT) {
+      const int wx = i % WX, wy = i / WX;
+      const int gx = (tx * TX + wx - 1 + P.nx) % P.nx;
+      const int gy = D3 ? (ty * TY + wy - 1 + P.ny) % P.ny : 0;
+      const int64_t idx = D3 ? ((int64_t)gm * P.ny + gy) * P.nx + gx : (int64_t)gm * P.nx + gx;
+      win[slot][wy][wx] = __ldcg(psi_g + idx);
+    }
+  };
+
+  __syncthreads();  // neighbour list ready
+  stage(0);
+  stage(1);
+  if (L_ > 2) stage(2);
+  wait(1, 1);  // chunk below: its last plane
+  wait(0, L_ > 2 ? 3 : 2);
+  if (ok) {
+    load_window(p0 - 1, 0);
+    load_window(p0, 1);
+  }
+  for (int k = 0; k < L_ && ok; ++k) {
+    if (k + 3 < L_) stage(k + 3);
+    // plane p0 + k + 1: same chunk up to the last plane, else the chunk above's first plane
+    if (k + 1 < L_)
+      wait(0, k + 3 < L_ ? k + 3 : L_);
+    else
+      wait(2, 2);
+    if (!ok) break;
+    load_window(p0 + k + 1, (k + 2) % 3);
+    __syncthreads();
+    const int m = p0 + k;
+    const int64_t idx = site_index(m);
+    Site st;
+    st.set(P, idx);
+    R pn[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      const int em = D3 ? L::e(a, 2) : L::e(a, 1);
+      const int ey = D3 ? L::e(a, 1) : 0;
+      pn[a] = (R)win[(k + 1 + em + 3) % 3][D3 ? ly + 1 + ey : 0][lx + 1 + L::e(a, 0)];
+    }
+    site_collide<Q, NC, Prec, MRT>(P, f, st, idx, parity, pn);
+  }
+  if (!ok) err |= ST_TIMEOUT;
+  // finish: the last block of the launch folds the pending status and advances the step
+  if (err) atomicOr(A.pending, err);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(A.done, 1u);
+    if (prev == gridDim.x - 1) {
+      __threadfence();
+      const int pend = *(volatile int*)A.pending;
+      if (pend)
+        *status |= pend;
+      else
+        *t_dev += 1;
+      *A.pending = 0;
+      *A.done = 0;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -344,6 +557,26 @@ struct Launch {
                       cudaStream_t s) {
     k_collide<Q, NC, Prec, MRT><<<blocks(P), kBlock, 0, s>>>(P, (S*)f, (const PsiT*)ps, st, t_dev, parity);
   }
+  static int fused_max_blocks() {
+    int nb = 0, dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fused<Q, NC, Prec, MRT>, Fused<Q>::NT, 0) !=
+        cudaSuccess)
+      return 0;
+    return nb * sms;
+  }
+  static cudaError_t fused(const Params& P, void* f, void* ps, int* st, long long* t_dev, const FusedArgs& A,
+                           cudaStream_t s) {
+    S* fp = (S*)f;
+    PsiT* pp = (PsiT*)ps;
+    Params Pc = P;
+    FusedArgs Ac = A;
+    void* args[] = {(void*)&Pc, (void*)&fp, (void*)&pp, (void*)&st, (void*)&t_dev, (void*)&Ac};
+    const unsigned grid = (unsigned)(A.ntx * A.nty * A.nchunk);
+    return cudaLaunchCooperativeKernel((const void*)k_fused<Q, NC, Prec, MRT>, dim3(grid), dim3(Fused<Q>::NT),
+                                       args, 0, s);
+  }
   static void init(const Params& P, void* f, const double* rho, const double* u, cudaStream_t s) {
     k_init<Q, NC, Prec><<<blocks(P), kBlock, 0, s>>>(P, (S*)f, rho, u);
   }
@@ -364,7 +597,9 @@ struct Launch {
     k_mass_final<<<1, kBlock, 0, s>>>(partial, (int)nb, NC, out);
   }
   static const Ops* table() {
-    static const Ops ops = {psi, collide, init, get_f, set_f, fields, mass, (int)sizeof(S), (int)sizeof(PsiT)};
+    static const Ops ops = {psi,    collide, fused, fused_max_blocks, init,           get_f,
+                            set_f,  fields,  mass,  (int)sizeof(S),   (int)sizeof(PsiT), Fused<Q>::TX,
+                            Fused<Q>::TY};
     return &ops;
   }
 };
@@ -378,12 +613,6 @@ const Ops* ops_nc(int nc) {
     case 4: return Launch<Q, 4, Prec, MRT>::table();
   }
   return nullptr;
-}
-
-template <int Q>
-const Ops* ops_for(int nc, int precision, int collision) {
-  if (precision == 0) return collision ? ops_nc<Q, PrecF64, 1>(nc) : ops_nc<Q, PrecF64, 0>(nc);
-  return collision ? ops_nc<Q, PrecF32S, 1>(nc) : ops_nc<Q, PrecF32S, 0>(nc);
 }
 
 }  // namespace lbm

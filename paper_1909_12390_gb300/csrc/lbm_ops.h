@@ -7,11 +7,15 @@
 namespace lbm {
 
 struct Params;
+struct FusedArgs;
 
 struct Ops {
   void (*psi)(const Params&, const void* f, void* psi, int* status, int parity, cudaStream_t);
   void (*collide)(const Params&, void* f, const void* psi, const int* status, long long* t_dev, int parity,
                   cudaStream_t);
+  cudaError_t (*fused)(const Params&, void* f, void* psi, int* status, long long* t_dev, const FusedArgs&,
+                       cudaStream_t);
+  int (*fused_max_blocks)();  // co-resident blocks of the fused kernel on this device
   void (*init)(const Params&, void* f, const double* rho, const double* u, cudaStream_t);
   void (*get_f)(const Params&, const void* f, double* out, int parity, cudaStream_t);
   void (*set_f)(const Params&, void* f, const double* in, cudaStream_t);
@@ -20,9 +24,13 @@ struct Ops {
   void (*mass)(const Params&, const void* f, double* partial, double* out, cudaStream_t);
   int store_bytes;  // bytes per stored population
   int psi_bytes;    // bytes per stored pseudo-potential value
+  int fused_tx;     // fused-kernel tile: sites along x
+  int fused_ty;     // and along y (1 for D2Q9)
 };
 
-const Ops* ops_q9(int nc, int precision, int collision);
-const Ops* ops_q19(int nc, int precision, int collision);
+const Ops* ops_q9_f64(int nc, int collision);
+const Ops* ops_q9_f32s(int nc, int collision);
+const Ops* ops_q19_f64(int nc, int collision);
+const Ops* ops_q19_f32s(int nc, int collision);
 
 }  // namespace lbm

@@ -22,7 +22,8 @@ FP64, FP32_SHIFTED = 0, 1
 EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_init", "lbm_step", "lbm_time",
            "lbm_fields", "lbm_mass", "lbm_get_f", "lbm_set_f", "lbm_state_bytes", "lbm_save",
            "lbm_restore", "lbm_last_error", "lbm_scale_to_lattice", "lbm_profile",
-           "lbm_profile_read")
+           "lbm_profile_read", "lbm_set_path", "lbm_get_path", "lbm_test_silence_block")
+PATH_AUTO, PATH_TWO_KERNEL, PATH_FUSED = 0, 1, 2
 
 
 class LBMError(RuntimeError):
@@ -79,6 +80,9 @@ def lib() -> ctypes.CDLL:
         L.lbm_restore.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int64]
         L.lbm_profile.argtypes = [vp, ctypes.c_int]
         L.lbm_profile_read.argtypes = [vp, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_int64)]
+        L.lbm_set_path.argtypes = [vp, ctypes.c_int]
+        L.lbm_get_path.argtypes = [vp]
+        L.lbm_test_silence_block.argtypes = [vp, ctypes.c_int]
         L.lbm_last_error.argtypes = [vp]
         L.lbm_last_error.restype = ctypes.c_char_p
         L.lbm_scale_to_lattice.argtypes = [ctypes.c_int, ctypes.POINTER(Component), ctypes.c_double,
@@ -203,11 +207,22 @@ class Lattice:
         a = _f64(f, self.nc * self.Q * self.N)
         self._check(lib().lbm_set_f(self._h, _dp(a)))
 
+    def set_path(self, path: int):
+        self._check(lib().lbm_set_path(self._h, int(path)))
+
+    @property
+    def path(self) -> int:
+        return int(lib().lbm_get_path(self._h))
+
+    def test_silence_block(self, block: int):
+        self._check(lib().lbm_test_silence_block(self._h, int(block)))
+
     def profile(self, on: bool):
         self._check(lib().lbm_profile(self._h, 1 if on else 0))
 
     def profile_read(self, kernel: int):
-        """(total milliseconds, launches) of kernel kind 0 (psi pass) or 1 (collide pass)."""
+        """(total milliseconds, launches) of kernel kind 0 (psi pass), 1 (collide pass) or 2
+        (fused step)."""
         ms = ctypes.c_double()
         n = ctypes.c_int64()
         self._check(lib().lbm_profile_read(self._h, kernel, ctypes.byref(ms), ctypes.byref(n)))

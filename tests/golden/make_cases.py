@@ -36,6 +36,7 @@ from oracle import thermo as th  # noqa: E402
 
 K_TO_R = 1.8
 PSIA_TO_MPA = 0.00689475729
+T_SPHERE = 0.95  # T / T_pc of the 3-component sphere
 
 # Critical constants: C1 and nC4 as stated for the workloads; C3 and nC5 from Table 1
 # (psia, degrees Rankine) converted to MPa and K.
@@ -73,32 +74,50 @@ def thermo_case(phys, z, tfrac, liquid_fraction, kij=None):
 
 def main():
     seed = lbm_inputs.DEFAULT_SEED
+    only = set(sys.argv[sys.argv.index("--only") + 1].split(",")) if "--only" in sys.argv else None
+    path = os.path.join(HERE, "cases.json")
     cases = {}
+    if only and os.path.exists(path):
+        with open(path) as fh:
+            cases = json.load(fh)
 
-    c = thermo_case([C1, NC4], [0.3, 0.7], 0.85, 0.5)
-    c.update(name="slab_d2q9_fp64_bgk", Q=9, shape=[64, 64], tau=1.0, beta=1.945,
+    def want(key):
+        return only is None or key in only
+
+    if want("c1"):
+        c = thermo_case([C1, NC4], [0.3, 0.7], 0.85, 0.5)
+        c.update(name="slab_d2q9_fp64_bgk", Q=9, shape=[64, 64], tau=1.0, beta=1.945,
              collision="bgk", precision="fp64", steps=2000,
-             init=dict(kind="slab", axis="y", lo=15.5, hi=47.5, width=4.0, noise=0.01, seed=seed))
-    cases["c1"] = c
+                 init=dict(kind="slab", axis="y", lo=15.5, hi=47.5, width=4.0, noise=0.01, seed=seed))
+        cases["c1"] = c
 
-    radius = lbm_inputs.droplet_radius(seed)
-    c = thermo_case([C1, C3, NC5], [0.2, 0.3, 0.5], 0.90, math.pi * radius ** 2 / 512 ** 2)
-    c.update(name="droplet_d2q9_fp32s_mrt", Q=9, shape=[512, 512], tau=0.8, beta=1.915,
-             collision="mrt", mrt_s=mrt_rates(9, 0.8), precision="fp32s", steps=20000,
-             init=dict(kind="ball", radius=radius, width=4.0))
-    cases["c2"] = c
+    if want("c2"):
+        radius = lbm_inputs.droplet_radius(seed)
+        c = thermo_case([C1, C3, NC5], [0.2, 0.3, 0.5], 0.90, math.pi * radius ** 2 / 512 ** 2)
+        c.update(name="droplet_d2q9_fp32s_mrt", Q=9, shape=[512, 512], tau=0.8, beta=1.915,
+                 collision="mrt", mrt_s=mrt_rates(9, 0.8), precision="fp32s", steps=20000,
+                 init=dict(kind="ball", radius=radius, width=4.0))
+        cases["c2"] = c
 
-    c = thermo_case([C1, C3, NC5], [0.2, 0.3, 0.5], 0.90, 4.0 / 3.0 * math.pi * 48 ** 3 / 256 ** 3)
-    c.update(name="sphere_d3q19_fp32s_mrt", Q=19, shape=[256, 256, 256], tau=0.8, beta=1.915,
-             collision="mrt", mrt_s=mrt_rates(19, 0.8), precision="fp32s", steps=5000,
-             init=dict(kind="ball", radius=48.0, width=4.0))
-    cases["c3"] = c
+    if want("c3"):
+        c = thermo_case([C1, C3, NC5], [0.2, 0.3, 0.5], T_SPHERE, 4.0 / 3.0 * math.pi * 48 ** 3 / 256 ** 3)
+        c.update(name="sphere_d3q19_fp32s_mrt", Q=19, shape=[256, 256, 256], tau=0.8, beta=1.915,
+                 collision="mrt", mrt_s=mrt_rates(19, 0.8), precision="fp32s", steps=5000,
+                 init=dict(kind="ball", radius=48.0, width=4.0))
+        cases["c3"] = c
 
-    c = thermo_case([C1, NC4], [0.3, 0.7], 0.85, math.pi * 64 ** 2 / 256 ** 2)
-    c.update(name="droplet_d2q9_fp32s_bgk_adjoint", Q=9, shape=[256, 256], tau=0.8, beta=1.915,
-             collision="bgk", precision="fp32s", steps=3000, checkpoint_every=55,
-             target_k12=0.02, init=dict(kind="ball", radius=64.0, width=4.0))
-    cases["c5"] = c
+    if want("c5"):
+        c = thermo_case([C1, NC4], [0.3, 0.7], 0.85, math.pi * 64 ** 2 / 256 ** 2)
+        c.update(name="droplet_d2q9_fp32s_bgk_adjoint", Q=9, shape=[256, 256], tau=0.8, beta=1.915,
+                 collision="bgk", precision="fp32s", steps=3000, checkpoint_every=55,
+                 target_k12=0.02, init=dict(kind="ball", radius=64.0, width=4.0))
+        cases["c5"] = c
+
+    if not want("c4"):
+        with open(path, "w") as fh:
+            json.dump(cases, fh, indent=1)
+        print("wrote", path)
+        return
 
     def feasible(d):
         try:
@@ -120,9 +139,9 @@ def main():
     cases["c4"] = dict(name="batched_flash_d2q9_fp32s_bgk", Q=9, tau=0.8, beta=1.945,
                        collision="bgk", precision="fp32s", steps=10000, cases=batch)
 
-    with open(os.path.join(HERE, "cases.json"), "w") as fh:
+    with open(path, "w") as fh:
         json.dump(cases, fh, indent=1)
-    print("wrote", os.path.join(HERE, "cases.json"))
+    print("wrote", path)
 
 
 if __name__ == "__main__":
