@@ -13,6 +13,7 @@
 
 #include "lbm.h"
 #include "lbm_core.cuh"
+#include "lbm_host.h"
 #include "lbm_kernels.cuh"
 #include "lbm_ops.h"
 
@@ -270,65 +271,66 @@ bool build_graph(lbm_ctx* c) {
 
 }  // namespace
 
-extern "C" {
+namespace lbm {
 
-lbm_status lbm_create(const lbm_grid* grid, int nc, const lbm_component* comps, const lbm_eos* eos,
-                      double tau, lbm_ctx** out) {
-  g_create_error.clear();
-  if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
-  *out = nullptr;
-  if (!grid || !comps || !eos) return fail(nullptr, LBM_ERR_ARG, "grid, comps and eos must be non-NULL");
+// Validates one lattice description and fills its kernel parameters (Section 3.2 component
+// parameters, mixing-rule products, MRT rates) and dispatch table. Touches no device state.
+lbm_status make_params(const lbm_grid* grid, int nc, const lbm_component* comps, const lbm_eos* eos, double tau,
+                       Params* out, const Ops** ops_out, std::string* why) {
+  auto bad = [&](const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    *why = buf;
+    return LBM_ERR_ARG;
+  };
+  if (!grid || !comps || !eos) return bad("grid, comps and eos must be non-NULL");
   if (grid->lattice != LBM_D2Q9 && grid->lattice != LBM_D3Q19)
-    return fail(nullptr, LBM_ERR_ARG, "lattice must be 9 (D2Q9) or 19 (D3Q19)");
-  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return fail(nullptr, LBM_ERR_ARG, "grid sizes must be >= 1");
-  if (grid->lattice == LBM_D2Q9 && grid->nz != 1) return fail(nullptr, LBM_ERR_ARG, "D2Q9 needs nz == 1");
+    return bad("lattice must be 9 (D2Q9) or 19 (D3Q19)");
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return bad("grid sizes must be >= 1");
+  if (grid->lattice == LBM_D2Q9 && grid->nz != 1) return bad("D2Q9 needs nz == 1");
   const int64_t N = (int64_t)grid->nx * grid->ny * grid->nz;
-  if (N > ((int64_t)1 << 40)) return fail(nullptr, LBM_ERR_ARG, "grid too large");
-  if (nc < 1 || nc > 4) return fail(nullptr, LBM_ERR_ARG, "nc must be 1..4");
-  if (!(tau > 0.5) || !std::isfinite(tau)) return fail(nullptr, LBM_ERR_ARG, "tau must be > 1/2");
+  if (N > ((int64_t)1 << 40)) return bad("grid too large");
+  if (nc < 1 || nc > 4) return bad("nc must be 1..4");
+  if (!(tau > 0.5) || !std::isfinite(tau)) return bad("tau must be > 1/2");
   if (eos->precision != LBM_FP64 && eos->precision != LBM_FP32_SHIFTED)
-    return fail(nullptr, LBM_ERR_ARG, "precision must be LBM_FP64 or LBM_FP32_SHIFTED");
+    return bad("precision must be LBM_FP64 or LBM_FP32_SHIFTED");
   if (eos->collision != LBM_BGK && eos->collision != LBM_MRT)
-    return fail(nullptr, LBM_ERR_ARG, "collision must be LBM_BGK or LBM_MRT");
-  if (eos->collision == LBM_MRT && !eos->mrt_rates) return fail(nullptr, LBM_ERR_ARG, "MRT needs mrt_rates");
-  if (!(eos->T > 0) || !std::isfinite(eos->T)) return fail(nullptr, LBM_ERR_ARG, "T must be > 0");
-  if (!(eos->G != 0) || !std::isfinite(eos->G)) return fail(nullptr, LBM_ERR_ARG, "G must be nonzero");
-  if (!std::isfinite(eos->beta)) return fail(nullptr, LBM_ERR_ARG, "beta must be finite");
+    return bad("collision must be LBM_BGK or LBM_MRT");
+  if (eos->collision == LBM_MRT && !eos->mrt_rates) return bad("MRT needs mrt_rates");
+  if (!(eos->T > 0) || !std::isfinite(eos->T)) return bad("T must be > 0");
+  if (!(eos->G != 0) || !std::isfinite(eos->G)) return bad("G must be nonzero");
+  if (!std::isfinite(eos->beta)) return bad("beta must be finite");
   const double R = eos->R == 0 ? 1.0 : eos->R;
-  if (!(R > 0) || !std::isfinite(R)) return fail(nullptr, LBM_ERR_ARG, "R must be > 0");
+  if (!(R > 0) || !std::isfinite(R)) return bad("R must be > 0");
   for (int i = 0; i < nc; ++i) {
     const lbm_component& k = comps[i];
     if (!(k.Tc > 0) || !(k.pc > 0) || !(k.M > 0) || !std::isfinite(k.omega) || !std::isfinite(k.Tc) ||
         !std::isfinite(k.pc) || !std::isfinite(k.M))
-      return fail(nullptr, LBM_ERR_ARG, "component %d: Tc, pc, M must be finite and > 0", i);
+      return bad("component %d: Tc, pc, M must be finite and > 0", i);
     if (eos->gamma && (!(eos->gamma[i] > 0) || !std::isfinite(eos->gamma[i])))
-      return fail(nullptr, LBM_ERR_ARG, "gamma[%d] must be finite and > 0", i);
+      return bad("gamma[%d] must be finite and > 0", i);
     if (eos->rho_ref && !std::isfinite(eos->rho_ref[i]))
-      return fail(nullptr, LBM_ERR_ARG, "rho_ref[%d] must be finite", i);
+      return bad("rho_ref[%d] must be finite", i);
     if (eos->kij)
       for (int j = 0; j < nc; ++j)
         if (!std::isfinite(eos->kij[i * nc + j]) || eos->kij[i * nc + j] != eos->kij[j * nc + i])
-          return fail(nullptr, LBM_ERR_ARG, "kij must be finite and symmetric");
+          return bad("kij must be finite and symmetric");
   }
   const int Q = grid->lattice;
   if (eos->collision == LBM_MRT)
     for (int k = 0; k < Q; ++k)
       if (!std::isfinite(eos->mrt_rates[k]) || !(eos->mrt_rates[k] > 0) || !(eos->mrt_rates[k] < 2))
-        return fail(nullptr, LBM_ERR_ARG, "mrt_rates[%d] must lie in (0, 2)", k);
+        return bad("mrt_rates[%d] must lie in (0, 2)", k);
   const bool f64 = eos->precision == LBM_FP64;
-  const lbm::Ops* ops = Q == 9 ? (f64 ? lbm::ops_q9_f64 : lbm::ops_q9_f32s)(nc, eos->collision)
-                               : (f64 ? lbm::ops_q19_f64 : lbm::ops_q19_f32s)(nc, eos->collision);
-  if (!ops) return fail(nullptr, LBM_ERR_ARG, "no kernels for this configuration");
+  const Ops* ops = Q == 9 ? (f64 ? ops_q9_f64 : ops_q9_f32s)(nc, eos->collision)
+                               : (f64 ? ops_q19_f64 : ops_q19_f32s)(nc, eos->collision);
+  if (!ops) return bad("no kernels for this configuration");
 
-  lbm_ctx* c = new (std::nothrow) lbm_ctx();
-  if (!c) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
-  c->grid = *grid;
-  c->nc = nc;
-  c->Q = Q;
-  c->precision = eos->precision;
-  c->collision = eos->collision;
-  c->ops = ops;
-  lbm::Params& P = c->P;
+  Params& P = *out;
+  P = Params{};
   P.nx = grid->nx;
   P.ny = grid->ny;
   P.nz = grid->nz;
@@ -364,7 +366,37 @@ lbm_status lbm_create(const lbm_grid* grid, int nc, const lbm_component* comps, 
   P.cpsi = 2.0 / (eos->G * (1.0 / 3.0));
   P.beta = eos->beta;
   P.G = eos->G;
+  *ops_out = ops;
+  return LBM_OK;
+}
+
+}  // namespace lbm
+
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_grid* grid, int nc, const lbm_component* comps, const lbm_eos* eos,
+                      double tau, lbm_ctx** out) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  lbm::Params P{};
+  const lbm::Ops* ops = nullptr;
+  std::string why;
+  lbm_status st = lbm::make_params(grid, nc, comps, eos, tau, &P, &ops, &why);
+  if (st != LBM_OK) return fail(nullptr, st, "%s", why.c_str());
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+  c->grid = *grid;
+  c->nc = nc;
+  c->Q = grid->lattice;
+  c->precision = eos->precision;
+  c->collision = eos->collision;
+  c->ops = ops;
+  c->P = P;
   c->ref_given = eos->rho_ref != nullptr;
+  const int Q = c->Q;
+  const int64_t N = P.N;
 
   cudaError_t e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&c->f, (size_t)nc * Q * N * ops->store_bytes);
