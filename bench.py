@@ -214,6 +214,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--path", default="auto", choices=["auto", "fused", "two"],
+                    help="step path of the timed run (default: the library's choice)")
     ap.add_argument("--grid", type=int, default=0,
                     help="cube edge of a smaller case of the same workload (profiling); 0 = 256")
     args = ap.parse_args()
@@ -246,6 +248,8 @@ def main():
     rho0 = init_fields(c)
 
     gpu = lattice_for(c, lbm.FP32_SHIFTED)
+    if args.path != "auto":
+        gpu.set_path(lbm.PATH_FUSED if args.path == "fused" else lbm.PATH_TWO_KERNEL)
     gpu.init(rho0)
     gpu.step(args.warmup)
     start = torch.cuda.Event(enable_timing=True)

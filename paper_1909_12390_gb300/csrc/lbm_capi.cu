@@ -195,8 +195,8 @@ void free_fused(lbm_ctx* c) {
 }
 
 // Chooses the fused tiling: tiles of fused_tx x fused_ty sites across the grid, the slowest
-// axis cut into the largest number of chunks (each >= 4 planes) whose blocks are still all
-// co-resident. Returns false when the grid does not tile or the blocks would not fit.
+// axis cut into the largest number of chunks (each at least two groups of fused_group planes)
+// whose blocks are still all co-resident. Returns false when the grid does not tile or the blocks would not fit.
 bool setup_fused(lbm_ctx* c) {
   free_fused(c);
   const int TX = c->ops->fused_tx, TY = c->ops->fused_ty;
@@ -207,9 +207,10 @@ bool setup_fused(lbm_ctx* c) {
   const int ntx = nx / TX, nty = d3 ? ny / TY : 1;
   const int cap = c->ops->fused_max_blocks();
   const long long tiles = (long long)ntx * nty;
+  const int NP = c->ops->fused_group;
   int best = 0;
   for (int nch = 1; nch <= nm; ++nch)
-    if (nm % nch == 0 && nm / nch >= 4 && tiles * nch <= cap) best = nch;
+    if (nm % (nch * NP) == 0 && nm / (nch * NP) >= 2 && tiles * nch <= cap) best = nch;
   if (best == 0) return false;
   const size_t nb = (size_t)tiles * best;
   lbm::FusedArgs a{};

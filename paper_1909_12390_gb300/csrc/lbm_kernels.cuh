@@ -240,12 +240,12 @@ __global__ void __launch_bounds__(kBlock, 2) k_collide(const Params P, typename 
 template <int Q>
 struct Fused;
 template <>
-struct Fused<19> {  // tile of 32 x 8 sites in (x, y), march along z
-  static constexpr int TX = 32, TY = 8, NT = TX * TY, WY = TY + 2;
+struct Fused<19> {  // tile of 32 x 8 sites in (x, y), march along z in groups of 4 planes
+  static constexpr int TX = 32, TY = 8, NT = TX * TY, WY = TY + 2, P = 4;
 };
 template <>
-struct Fused<9> {  // tile of 128 sites in x, march along y
-  static constexpr int TX = 128, TY = 1, NT = TX, WY = 1;
+struct Fused<9> {  // tile of 128 sites in x, march along y in groups of 4 rows
+  static constexpr int TX = 128, TY = 1, NT = TX, WY = 1, P = 4;
 };
 
 struct FusedArgs {
@@ -267,17 +267,26 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// One launch = one time step. Block b owns tile (tx, ty) of chunk ch: planes [p0, p0 + L) of
+// the march axis (z for D3Q19, y for D2Q9), in G = L / P groups of P planes. Stage s computes
+// psi of one group and publishes it (progress counter = base + s + 1): stage 0 is the chunk's
+// last group (needed first by the chunk above), stage s >= 1 is group s - 1. Colliding group j
+// needs psi of the plane below and above the group, from this and the neighbouring tiles, so
+// it waits for the neighbours' counters to reach min(j + 3, G) (the chunk below's last group
+// for j = 0, the chunk above's first group for j = G - 1). Stages never wait, so every wait
+// refers to work that does not depend on the waiter: with all blocks co-resident the
+// pipeline cannot deadlock, and every wait is bounded anyway.
 template <int Q, int NC, class Prec, int MRT>
 __global__ void __launch_bounds__(Fused<Q>::NT, Q == 19 ? 2 : 4)
     k_fused(const Params P, typename Prec::S* __restrict__ f, typename Prec::PsiT* __restrict__ psi_g, int* status,
             long long* t_dev, const FusedArgs A) {
-  using G = Fused<Q>;
+  using Gm = Fused<Q>;
   using R = typename Prec::R;
   using PsiT = typename Prec::PsiT;
   using L = Lat<Q>;
   constexpr bool D3 = Q == 19;
-  constexpr int TX = G::TX, TY = G::TY, WY = G::WY, WX = TX + 2;
-  __shared__ PsiT win[3][WY][WX];
+  constexpr int TX = Gm::TX, TY = Gm::TY, WY = Gm::WY, WX = TX + 2, NP = Gm::P, NS = NP + 2;
+  __shared__ PsiT win[NS][WY][WX];
   __shared__ int nbr[27];
   __shared__ int nbr_need[27];  // 0 = same chunk, 1 = chunk below, 2 = chunk above
   __shared__ int n_nbr;
@@ -285,8 +294,8 @@ __global__ void __launch_bounds__(Fused<Q>::NT, Q == 19 ? 2 : 4)
   if (*(volatile int*)status) return;  // a previous step failed: do nothing
   const unsigned long long t = (unsigned long long)*(volatile long long*)t_dev;
   const int parity = (int)(t & 1);
-  const int L_ = A.L;
-  const unsigned long long base = t * (unsigned long long)L_;
+  const int L_ = A.L, G = A.L / NP;
+  const unsigned long long base = t * (unsigned long long)G;
   const int b = blockIdx.x;
   const int tx = b % A.ntx;
   const int ty = (b / A.ntx) % A.nty;
@@ -317,15 +326,20 @@ __global__ void __launch_bounds__(Fused<Q>::NT, Q == 19 ? 2 : 4)
     return D3 ? ((int64_t)m * P.ny + cy) * P.nx + cx : (int64_t)m * P.nx + cx;
   };
   int err = 0;
-  // stage s computes psi of plane p(s): s = 0 the chunk's last plane, s >= 1 plane p0 + s - 1
+  // stage s: psi of the NP planes of group (s == 0 ? G - 1 : s - 1)
   auto stage = [&](int s_) {
-    const int m = s_ == 0 ? p0 + L_ - 1 : p0 + s_ - 1;
-    const int64_t idx = site_index(m);
-    Site st;
-    st.set(P, idx);
-    PsiT v;
-    err |= site_psi<Q, NC, Prec>(P, f, st, idx, parity, v);
-    psi_g[idx] = v;
+    const int g = s_ == 0 ? G - 1 : s_ - 1;
+    PsiT v[NP];
+    int64_t ix[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      ix[i] = site_index(p0 + g * NP + i);
+      Site st;
+      st.set(P, ix[i]);
+      err |= site_psi<Q, NC, Prec>(P, f, st, ix[i], parity, v[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) psi_g[ix[i]] = v[i];
     __syncthreads();
     if (threadIdx.x == 0 && b != A.silent_block) st_release_u64(&A.flags[b], base + (unsigned long long)(s_ + 1));
   };
@@ -347,10 +361,12 @@ __global__ void __launch_bounds__(Fused<Q>::NT, Q == 19 ? 2 : 4)
     }
     ok = __syncthreads_and(mine && ok) != 0;
   };
-  // psi window of plane m (periodic) into slot, through L2 (written by other blocks)
-  auto load_window = [&](int m, int slot) {
-    const int gm = (m % nm + nm) % nm;
-    for (int i = threadIdx.x; i < WY * WX; i += G::NT) {
+  // psi of plane p0 + q (q may be -1 or L: the neighbouring chunks) into its ring slot, through
+  // L2 (written by other blocks)
+  auto load_plane = [&](int q) {
+    const int gm = ((p0 + q) % nm + nm) % nm;
+    const int slot = (q + 1 + NS) % NS;
+    for (int i = threadIdx.x; i < WY * WX; i += Gm::NT) {
       const int wx = i % WX, wy = i / WX;
       const int gx = (tx * TX + wx - 1 + P.nx) % P.nx;
       const int gy = D3 ? (ty * TY + wy - 1 + P.ny) % P.ny : 0;
@@ -362,35 +378,36 @@ __global__ void __launch_bounds__(Fused<Q>::NT, Q == 19 ? 2 : 4)
   __syncthreads();  // neighbour list ready
   stage(0);
   stage(1);
-  if (L_ > 2) stage(2);
-  wait(1, 1);  // chunk below: its last plane
-  wait(0, L_ > 2 ? 3 : 2);
+  if (G > 2) stage(2);
+  wait(1, 1);  // chunk below: its last group
   if (ok) {
-    load_window(p0 - 1, 0);
-    load_window(p0, 1);
+    load_plane(-1);
+    load_plane(0);
   }
-  for (int k = 0; k < L_ && ok; ++k) {
-    if (k + 3 < L_) stage(k + 3);
-    // plane p0 + k + 1: same chunk up to the last plane, else the chunk above's first plane
-    if (k + 1 < L_)
-      wait(0, k + 3 < L_ ? k + 3 : L_);
-    else
-      wait(2, 2);
+  for (int j = 0; j < G && ok; ++j) {
+    if (j + 3 < G) stage(j + 3);
+    // planes p0 + jP + 1 .. p0 + jP + NP: groups j and j + 1 of this chunk, or the chunk
+    // above's first group for the last group
+    wait(0, j + 3 < G ? j + 3 : G);
+    if (j == G - 1) wait(2, 2);
     if (!ok) break;
-    load_window(p0 + k + 1, (k + 2) % 3);
+    for (int i = 1; i <= NP; ++i) load_plane(j * NP + i);
     __syncthreads();
-    const int m = p0 + k;
-    const int64_t idx = site_index(m);
-    Site st;
-    st.set(P, idx);
-    R pn[Q];
+#pragma unroll 1
+    for (int i = 0; i < NP; ++i) {
+      const int q = j * NP + i;
+      const int64_t idx = site_index(p0 + q);
+      Site st;
+      st.set(P, idx);
+      R pn[Q];
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
-      const int em = D3 ? L::e(a, 2) : L::e(a, 1);
-      const int ey = D3 ? L::e(a, 1) : 0;
-      pn[a] = (R)win[(k + 1 + em + 3) % 3][D3 ? ly + 1 + ey : 0][lx + 1 + L::e(a, 0)];
+      for (int a = 0; a < Q; ++a) {
+        const int em = D3 ? L::e(a, 2) : L::e(a, 1);
+        const int ey = D3 ? L::e(a, 1) : 0;
+        pn[a] = (R)win[(q + 1 + em + NS) % NS][D3 ? ly + 1 + ey : 0][lx + 1 + L::e(a, 0)];
+      }
+      site_collide<Q, NC, Prec, MRT>(P, f, st, idx, parity, pn);
     }
-    site_collide<Q, NC, Prec, MRT>(P, f, st, idx, parity, pn);
   }
   if (!ok) err |= ST_TIMEOUT;
   // finish: the last block of the launch folds the pending status and advances the step
@@ -597,9 +614,9 @@ struct Launch {
     k_mass_final<<<1, kBlock, 0, s>>>(partial, (int)nb, NC, out);
   }
   static const Ops* table() {
-    static const Ops ops = {psi,    collide, fused, fused_max_blocks, init,           get_f,
-                            set_f,  fields,  mass,  (int)sizeof(S),   (int)sizeof(PsiT), Fused<Q>::TX,
-                            Fused<Q>::TY};
+    static const Ops ops = {psi,           collide,           fused,        fused_max_blocks, init,
+                            get_f,         set_f,             fields,       mass,             (int)sizeof(S),
+                            (int)sizeof(PsiT), Fused<Q>::TX, Fused<Q>::TY, Fused<Q>::P};
     return &ops;
   }
 };

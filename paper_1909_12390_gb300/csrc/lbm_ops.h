@@ -26,6 +26,7 @@ struct Ops {
   int psi_bytes;    // bytes per stored pseudo-potential value
   int fused_tx;     // fused-kernel tile: sites along x
   int fused_ty;     // and along y (1 for D2Q9)
+  int fused_group;  // planes per synchronisation round
 };
 
 const Ops* ops_q9_f64(int nc, int collision);
