@@ -172,6 +172,37 @@ lbm_status lbm_test_silence_block(lbm_ctx *ctx, int block);
 lbm_status lbm_profile(lbm_ctx *ctx, int on);
 lbm_status lbm_profile_read(lbm_ctx *ctx, int kernel, double *total_ms, int64_t *launches);
 
+/* Allocation-free step (the paper has no counterpart; this is a library service).
+ *
+ * Some callers cannot let a library allocate device memory: applications whose device
+ * memory is owned by their own pool allocator (a framework or runtime that reserves the GPU's
+ * memory up front, where an outside cudaMalloc fails or fragments the pool), and code that
+ * must not allocate at a given point because cudaMalloc and cudaFree can synchronise the
+ * device and stall other streams. lbm_step_static serves them: it advances n steps of one
+ * lattice (two-kernel path) on populations the caller keeps in its own device memory and
+ * calls no cudaMalloc, cudaFree or any other allocating routine.
+ *
+ * f_device holds the populations in the library's storage layout: f[nc][Q][N] structure of
+ * arrays, FP64, or FP32 holding f - w_a rho_ref_s when eos->precision is LBM_FP32_SHIFTED
+ * (eos->rho_ref gives the shift; NULL means 0), in the in-place streaming layout of step t0
+ * (even t0: slot (x, a) holds f_a(x); lbm_save writes this layout). The other arguments are
+ * those of lbm_create. On return *t_out (if not NULL) is the number of completed steps.
+ *
+ * Scratch: the pseudo-potential, the status word and the step counter live in one fixed
+ * device array inside the library, 256 B + LBM_STATIC_MAX_SITES * 8 B (8 MiB + 256 B), which
+ * every GPU that loads the library holds until the process exits. Grids with more than
+ * LBM_STATIC_MAX_SITES sites are rejected with LBM_ERR_ARG. The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture. Every call shares the array and leaves its contents
+ * behind; each call resets the status word and counter it uses. Calls whose work overlaps on
+ * the GPU (other streams or threads on the same device) race on the array: serialise them.
+ * The call synchronises `stream` (a cudaStream_t, NULL = default stream) before returning
+ * the first failing step's status. lbm_step_static_error gives this thread's last message. */
+#define LBM_STATIC_MAX_SITES 1048576
+lbm_status lbm_step_static(const lbm_grid *grid, int nc, const lbm_component *comps, const lbm_eos *eos,
+                           double tau, void *f_device, int64_t t0, int64_t n, void *stream, int64_t *t_out);
+const char *lbm_step_static_error(void);
+
 /* One-line description of the last failure of ctx ("" if none). Valid until the next call
  * on ctx. With ctx == NULL, the last failure of lbm_create. */
 const char *lbm_last_error(const lbm_ctx *ctx);

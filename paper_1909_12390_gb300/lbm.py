@@ -22,7 +22,9 @@ FP64, FP32_SHIFTED = 0, 1
 EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_init", "lbm_step", "lbm_time",
            "lbm_fields", "lbm_mass", "lbm_get_f", "lbm_set_f", "lbm_state_bytes", "lbm_save",
            "lbm_restore", "lbm_last_error", "lbm_scale_to_lattice", "lbm_profile",
-           "lbm_profile_read", "lbm_set_path", "lbm_get_path", "lbm_test_silence_block")
+           "lbm_profile_read", "lbm_set_path", "lbm_get_path", "lbm_test_silence_block",
+           "lbm_step_static", "lbm_step_static_error")
+STATIC_MAX_SITES = 1048576
 PATH_AUTO, PATH_TWO_KERNEL, PATH_FUSED = 0, 1, 2
 
 
@@ -83,6 +85,11 @@ def lib() -> ctypes.CDLL:
         L.lbm_set_path.argtypes = [vp, ctypes.c_int]
         L.lbm_get_path.argtypes = [vp]
         L.lbm_test_silence_block.argtypes = [vp, ctypes.c_int]
+        L.lbm_step_static.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.POINTER(Component),
+                                      ctypes.POINTER(Eos), ctypes.c_double, vp, ctypes.c_int64, ctypes.c_int64,
+                                      vp, ctypes.POINTER(ctypes.c_int64)]
+        L.lbm_step_static_error.argtypes = []
+        L.lbm_step_static_error.restype = ctypes.c_char_p
         L.lbm_last_error.argtypes = [vp]
         L.lbm_last_error.restype = ctypes.c_char_p
         L.lbm_scale_to_lattice.argtypes = [ctypes.c_int, ctypes.POINTER(Component), ctypes.c_double,
@@ -104,6 +111,43 @@ def _f64(a, n=None):
     return a
 
 
+def make_args(shape, components, T, gamma=None, kij=None, beta=1.0, G=-1.0, collision=BGK,
+              mrt_rates=None, precision=FP64, rho_ref=None, R=1.0):
+    """The lbm_grid, lbm_component[] and lbm_eos of one lattice (plus arrays to keep alive)."""
+    shape = tuple(int(s) for s in shape)
+    Q = D2Q9 if len(shape) == 2 else D3Q19
+    nx, ny = shape[0], shape[1]
+    nz = shape[2] if len(shape) == 3 else 1
+    nc = len(components)
+    comps = (Component * nc)(*[Component(*c) for c in components])
+    keep = []
+
+    def arr(v, n):
+        if v is None:
+            return None
+        a = _f64(v, n)
+        keep.append(a)
+        return _dp(a)
+
+    eos = Eos(T=T, R=R, kij=arr(None if kij is None else np.asarray(kij, dtype=float).ravel(), nc * nc),
+              gamma=arr(gamma, nc), beta=beta, G=G, collision=collision,
+              mrt_rates=arr(mrt_rates, Q), precision=precision, rho_ref=arr(rho_ref, nc))
+    return Grid(nx, ny, nz, Q), comps, eos, keep
+
+
+def step_static(shape, components, T, tau, f_device_ptr: int, t0: int, n: int, stream: int = 0, **kw):
+    """lbm_step_static on caller-owned device populations at address f_device_ptr; returns the
+    number of completed steps. Raises LBMError on failure."""
+    grid, comps, eos, keep = make_args(shape, components, T, **kw)
+    tout = ctypes.c_int64()
+    st = lib().lbm_step_static(ctypes.byref(grid), len(components), comps, ctypes.byref(eos), tau,
+                               ctypes.c_void_p(f_device_ptr), int(t0), int(n), ctypes.c_void_p(stream or None),
+                               ctypes.byref(tout))
+    if st != OK:
+        raise LBMError(st, lib().lbm_step_static_error().decode())
+    return tout.value
+
+
 class Lattice:
     """One periodic lattice with nc components, behind lbm_create / lbm_destroy.
 
@@ -113,31 +157,18 @@ class Lattice:
     def __init__(self, shape, components, T, tau, gamma=None, kij=None, beta=1.0, G=-1.0,
                  collision=BGK, mrt_rates=None, precision=FP64, rho_ref=None, R=1.0):
         L = lib()
+        grid, comps, eos, keep = make_args(shape, components, T, gamma=gamma, kij=kij, beta=beta, G=G,
+                                           collision=collision, mrt_rates=mrt_rates, precision=precision,
+                                           rho_ref=rho_ref, R=R)
+        self._keep = keep
         shape = tuple(int(s) for s in shape)
-        self.Q = D2Q9 if len(shape) == 2 else D3Q19
-        nx, ny = shape[0], shape[1]
-        nz = shape[2] if len(shape) == 3 else 1
+        self.Q = grid.lattice
         self.shape = shape
         self.grid = tuple(reversed(shape))
-        self.N = nx * ny * nz
-        nc = len(components)
-        self.nc = nc
-        comps = (Component * nc)(*[Component(*c) for c in components])
-        self._keep = []
-
-        def arr(v, n):
-            if v is None:
-                return None
-            a = _f64(v, n)
-            self._keep.append(a)
-            return _dp(a)
-
-        eos = Eos(T=T, R=R, kij=arr(None if kij is None else np.asarray(kij, dtype=float).ravel(), nc * nc),
-                  gamma=arr(gamma, nc), beta=beta, G=G, collision=collision,
-                  mrt_rates=arr(mrt_rates, self.Q), precision=precision, rho_ref=arr(rho_ref, nc))
+        self.N = grid.nx * grid.ny * grid.nz
+        self.nc = len(components)
         h = ctypes.c_void_p()
-        st = L.lbm_create(ctypes.byref(Grid(nx, ny, nz, self.Q)), nc, comps, ctypes.byref(eos), tau,
-                          ctypes.byref(h))
+        st = L.lbm_create(ctypes.byref(grid), self.nc, comps, ctypes.byref(eos), tau, ctypes.byref(h))
         if st != OK:
             raise LBMError(st, L.lbm_last_error(None).decode())
         self._h = h
