@@ -172,6 +172,38 @@ lbm_status lbm_test_silence_block(lbm_ctx *ctx, int block);
 lbm_status lbm_profile(lbm_ctx *ctx, int on);
 lbm_status lbm_profile_read(lbm_ctx *ctx, int kernel, double *total_ms, int64_t *launches);
 
+/* ---- Batched lattices -------------------------------------------------------------------
+ * Many small independent D2Q9 cases (each its own grid, components' constants, temperature,
+ * kij, gamma, tau) advanced together, as in a sweep of flash conditions. All cases share nc,
+ * precision and collision. Each case is owned by one thread block that keeps the case's
+ * populations and pseudo-potential in shared memory for a whole chunk of steps (cases too
+ * large for shared memory run from global memory); cases are grouped by size, one launch per
+ * size class on its own stream, and the step loop replays a captured CUDA graph. Cases are
+ * independent: a case that fails (EOS domain, non-finite) stops at its failing step while the
+ * others continue. Arrays are indexed by case and concatenated in case order: grids[ncase],
+ * comps[ncase * nc], eos[ncase], tau[ncase]; fields rho[sum_c nc N_c] with case c at offset
+ * nc * (sites of cases before c), u likewise with 3 per site, p with 1 per site. */
+typedef struct lbm_batch lbm_batch;
+lbm_status lbm_batch_create(int ncase, const lbm_grid *grids, int nc, const lbm_component *comps,
+                            const lbm_eos *eos, const double *tau, lbm_batch **out);
+void lbm_batch_destroy(lbm_batch *b);
+/* Equilibrium start of every case from concatenated densities (and velocities or NULL). */
+lbm_status lbm_batch_init(lbm_batch *b, const double *rho, const double *u);
+/* Advances every case n steps; returns the first failing case's status (others still ran). */
+lbm_status lbm_batch_step(lbm_batch *b, int64_t n);
+/* Per-case status and step count (either array may be NULL). */
+lbm_status lbm_batch_case_status(lbm_batch *b, int *status, int64_t *t);
+lbm_status lbm_batch_fields(lbm_batch *b, double *rho, double *u, double *p);
+/* Canonical FP64 populations f[nc][9][N_c] of case i. */
+lbm_status lbm_batch_get_f(lbm_batch *b, int i, double *f);
+/* Autotuner: times trial_steps steps of every feasible block size per size class on the
+ * current state (restored afterwards) and keeps the fastest; lbm_batch_tune_report lists the
+ * choices. */
+lbm_status lbm_batch_tune(lbm_batch *b, int trial_steps);
+const char *lbm_batch_tune_report(const lbm_batch *b);
+int64_t lbm_batch_sites(const lbm_batch *b);
+const char *lbm_batch_last_error(const lbm_batch *b);
+
 /* Allocation-free step (the paper has no counterpart; this is a library service).
  *
  * Some callers cannot let a library allocate device memory: applications whose device

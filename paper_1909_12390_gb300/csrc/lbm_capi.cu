@@ -367,6 +367,7 @@ lbm_status make_params(const lbm_grid* grid, int nc, const lbm_component* comps,
   P.cpsi = 2.0 / (eos->G * (1.0 / 3.0));
   P.beta = eos->beta;
   P.G = eos->G;
+  finalize_params(P);
   *ops_out = ops;
   return LBM_OK;
 }
@@ -488,6 +489,7 @@ lbm_status lbm_init(lbm_ctx* c, const double* rho, const double* u) {
       if (!std::isfinite(u[i])) return fail(c, LBM_ERR_ARG, "u must be finite");
   if (c->precision == LBM_FP32_SHIFTED && !c->ref_given) {
     for (int s = 0; s < c->nc; ++s) c->P.rho_ref[s] = mean[s];
+    lbm::finalize_params(c->P);
     drop_graph(c);  // the graph holds the parameters by value
   }
   lbm_status st = ensure_scratch(c);

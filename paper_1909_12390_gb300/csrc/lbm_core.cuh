@@ -126,6 +126,53 @@ struct Params {
   double rho_ref[4]; // FP32 shift references (0 for FP64 storage)
   double gamma[4];
   double beta, G;
+  // constants derived by finalize_params(), in both precisions, so that no kernel converts a
+  // parameter per site (an FP64 -> FP32 conversion runs on GB300's 1/72-rate FP64 pipe)
+  double gk, c1, c2;  // 1 - omega/2, -beta G, -(1 - beta) G / 2
+  float omega_f, gk_f, c1_f, c2_f, cpsi_f;
+  float lam_f[10], rho_ref_f[4], gamma_f[4];
+};
+
+// Fills the derived constants of P (call after any change of omega, lam, rho_ref, gamma,
+// beta, G or cpsi).
+inline void finalize_params(Params& P) {
+  P.gk = 1.0 - 0.5 * P.omega;
+  P.c1 = -P.beta * P.G;
+  P.c2 = -0.5 * (1.0 - P.beta) * P.G;
+  P.omega_f = (float)P.omega;
+  P.gk_f = (float)P.gk;
+  P.c1_f = (float)P.c1;
+  P.c2_f = (float)P.c2;
+  P.cpsi_f = (float)P.cpsi;
+  for (int i = 0; i < 10; ++i) P.lam_f[i] = (float)P.lam[i];
+  for (int i = 0; i < 4; ++i) {
+    P.rho_ref_f[i] = (float)P.rho_ref[i];
+    P.gamma_f[i] = (float)P.gamma[i];
+  }
+}
+
+// Per-site constants in the arithmetic precision R of a kernel.
+template <class R>
+struct PC;
+template <>
+struct PC<double> {
+  __device__ __forceinline__ static double omega(const Params& P) { return P.omega; }
+  __device__ __forceinline__ static double gk(const Params& P) { return P.gk; }
+  __device__ __forceinline__ static double c1(const Params& P) { return P.c1; }
+  __device__ __forceinline__ static double c2(const Params& P) { return P.c2; }
+  __device__ __forceinline__ static double lam(const Params& P, int i) { return P.lam[i]; }
+  __device__ __forceinline__ static double rho_ref(const Params& P, int i) { return P.rho_ref[i]; }
+  __device__ __forceinline__ static double gamma(const Params& P, int i) { return P.gamma[i]; }
+};
+template <>
+struct PC<float> {
+  __device__ __forceinline__ static float omega(const Params& P) { return P.omega_f; }
+  __device__ __forceinline__ static float gk(const Params& P) { return P.gk_f; }
+  __device__ __forceinline__ static float c1(const Params& P) { return P.c1_f; }
+  __device__ __forceinline__ static float c2(const Params& P) { return P.c2_f; }
+  __device__ __forceinline__ static float lam(const Params& P, int i) { return P.lam_f[i]; }
+  __device__ __forceinline__ static float rho_ref(const Params& P, int i) { return P.rho_ref_f[i]; }
+  __device__ __forceinline__ static float gamma(const Params& P, int i) { return P.gamma_f[i]; }
 };
 
 // Status bits raised by kernels (OR-ed into one device word).

@@ -58,7 +58,7 @@ __device__ __forceinline__ int site_psi(const Params& P, const typename Prec::S*
     float rc[NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-      rc[i] = (float)P.rho_ref[i] + d[i];
+      rc[i] = P.rho_ref_f[i] + d[i];
       rho_t += rc[i];
     }
     EosOut<NC> e = eos_pr_f32in<NC>(P, rc);
@@ -69,7 +69,7 @@ __device__ __forceinline__ int site_psi(const Params& P, const typename Prec::S*
     psi2 = P.cpsi * (pD / Dd - rho_t * (1.0 / 3.0));
   } else {
     // the quotient and everything after it are well conditioned: FP32, like the stored psi
-    psi2 = (float)P.cpsi * ((float)pD / (float)Dd - rho_t * (1.0f / 3.0f));
+    psi2 = P.cpsi_f * ((float)pD / (float)Dd - rho_t * (1.0f / 3.0f));
   }
   psi_out = 0;
   if (!isfinite(psi2) || !isfinite(rho_t)) return ST_NONFINITE;
@@ -99,7 +99,7 @@ __device__ __forceinline__ void site_collide(const Params& P, typename Prec::S* 
       if (L::e(a, d) < 0) { s1[d] -= wp; s2[d] -= wq; }
     }
   }
-  const R c1 = (R)(-P.beta * P.G), c2 = (R)(-0.5 * (1.0 - P.beta) * P.G);
+  const R c1 = PC<R>::c1(P), c2 = PC<R>::c2(P);
   R F[3] = {0, 0, 0};
 #pragma unroll
   for (int d = 0; d < D; ++d) F[d] = c1 * pn[0] * s1[d] + c2 * s2[d];
@@ -123,9 +123,9 @@ __device__ __forceinline__ void site_collide(const Params& P, typename Prec::S* 
   R rc[NC], rho = 0, gs = 0;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    rc[c] = (R)P.rho_ref[c] + dl[c];
+    rc[c] = PC<R>::rho_ref(P, c) + dl[c];
     rho += rc[c];
-    gs += (R)P.gamma[c] * rc[c];
+    gs += PC<R>::gamma(P, c) * rc[c];
   }
   // barycentric velocity with the Guo half force
   R u[3] = {0, 0, 0};
@@ -154,11 +154,11 @@ __device__ __forceinline__ void site_collide(const Params& P, typename Prec::S* 
     Fb[a] = (R)L::w(a) * ((R)3 * (eF - uF) + (R)9 * eu * eF);
   }
 
-  const R om = (R)P.omega;
-  const R gk = (R)1 - (R)0.5 * om;
+  const R om = PC<R>::omega(P);
+  const R gk = PC<R>::gk(P);
   const R igs = (R)1 / gs;
   For<0, NC>::run([&]<int C>() {
-    const R chi = (R)P.gamma[C] * rc[C] * igs;  // S5
+    const R chi = PC<R>::gamma(P, C) * rc[C] * igs;  // S5
     R g[Q], out[Q];
     For<0, Q>::run([&]<int A>() {
       const R v = (R)f[AA<Q>::template read_slot<A>(P, s, idx, parity, C)];
@@ -179,7 +179,7 @@ __device__ __forceinline__ void site_collide(const Params& P, typename Prec::S* 
         for (int a = 0; a < Q; ++a) {
           if (L::m(k, a) != 0) mq += (R)L::m(k, a) * q[a];
         }
-        mq *= (R)P.lam[i];
+        mq *= PC<R>::lam(P, i);
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
           if (L::m(k, a) != 0) out[a] -= (R)L::m(k, a) * mq;
@@ -273,9 +273,13 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 // last group (needed first by the chunk above), stage s >= 1 is group s - 1. Colliding group j
 // needs psi of the plane below and above the group, from this and the neighbouring tiles, so
 // it waits for the neighbours' counters to reach min(j + 3, G) (the chunk below's last group
-// for j = 0, the chunk above's first group for j = G - 1). Stages never wait, so every wait
-// refers to work that does not depend on the waiter: with all blocks co-resident the
-// pipeline cannot deadlock, and every wait is bounded anyway.
+// for j = 0, the chunk above's first group for j = G - 1). Iteration j first computes stage
+// j + 2 (group j + 1), then waits, then collides group j: a stage never waits within its own
+// iteration and every wait refers to stages the neighbours compute before their own wait of
+// the same iteration, so with all blocks co-resident the pipeline cannot deadlock (and every
+// wait is bounded anyway). Group j + 1 is read for its psi one iteration before it is
+// collided, so its populations are re-read from L2 (a look-ahead of P planes over the whole
+// grid cross-section: 60 MB for 256^2 sites and 3 FP32 D3Q19 components).
 template <int Q, int NC, class Prec, int MRT>
 __global__ void __launch_bounds__(Fused<Q>::NT, Q == 19 ? 2 : 4)
     k_fused(const Params P, typename Prec::S* __restrict__ f, typename Prec::PsiT* __restrict__ psi_g, int* status,
@@ -379,13 +383,14 @@ __global__ void __launch_bounds__(Fused<Q>::NT, Q == 19 ? 2 : 4)
   stage(0);
   stage(1);
   if (G > 2) stage(2);
-  wait(1, 1);  // chunk below: its last group
+  wait(1, 1);  // chunk below: its last group (plane p0 - 1)
+  wait(0, 2);  // this chunk's tiles: group 0 (plane p0)
   if (ok) {
     load_plane(-1);
     load_plane(0);
   }
   for (int j = 0; j < G && ok; ++j) {
-    if (j + 3 < G) stage(j + 3);
+    if (j >= 1 && j + 2 < G) stage(j + 2);
     // planes p0 + jP + 1 .. p0 + jP + NP: groups j and j + 1 of this chunk, or the chunk
     // above's first group for the last group
     wait(0, j + 3 < G ? j + 3 : G);

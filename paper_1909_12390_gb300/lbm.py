@@ -23,7 +23,10 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_init", "lbm_step"
            "lbm_fields", "lbm_mass", "lbm_get_f", "lbm_set_f", "lbm_state_bytes", "lbm_save",
            "lbm_restore", "lbm_last_error", "lbm_scale_to_lattice", "lbm_profile",
            "lbm_profile_read", "lbm_set_path", "lbm_get_path", "lbm_test_silence_block",
-           "lbm_step_static", "lbm_step_static_error")
+           "lbm_step_static", "lbm_step_static_error", "lbm_batch_create", "lbm_batch_destroy",
+           "lbm_batch_init", "lbm_batch_step", "lbm_batch_case_status", "lbm_batch_fields",
+           "lbm_batch_get_f", "lbm_batch_tune", "lbm_batch_tune_report", "lbm_batch_sites",
+           "lbm_batch_last_error")
 STATIC_MAX_SITES = 1048576
 PATH_AUTO, PATH_TWO_KERNEL, PATH_FUSED = 0, 1, 2
 
@@ -90,6 +93,22 @@ def lib() -> ctypes.CDLL:
                                       vp, ctypes.POINTER(ctypes.c_int64)]
         L.lbm_step_static_error.argtypes = []
         L.lbm_step_static_error.restype = ctypes.c_char_p
+        L.lbm_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(Grid), ctypes.c_int,
+                                       ctypes.POINTER(Component), ctypes.POINTER(Eos), _DP, ctypes.POINTER(vp)]
+        L.lbm_batch_destroy.argtypes = [vp]
+        L.lbm_batch_destroy.restype = None
+        L.lbm_batch_init.argtypes = [vp, _DP, _DP]
+        L.lbm_batch_step.argtypes = [vp, ctypes.c_int64]
+        L.lbm_batch_case_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]
+        L.lbm_batch_fields.argtypes = [vp, _DP, _DP, _DP]
+        L.lbm_batch_get_f.argtypes = [vp, ctypes.c_int, _DP]
+        L.lbm_batch_tune.argtypes = [vp, ctypes.c_int]
+        L.lbm_batch_tune_report.argtypes = [vp]
+        L.lbm_batch_tune_report.restype = ctypes.c_char_p
+        L.lbm_batch_sites.argtypes = [vp]
+        L.lbm_batch_sites.restype = ctypes.c_int64
+        L.lbm_batch_last_error.argtypes = [vp]
+        L.lbm_batch_last_error.restype = ctypes.c_char_p
         L.lbm_last_error.argtypes = [vp]
         L.lbm_last_error.restype = ctypes.c_char_p
         L.lbm_scale_to_lattice.argtypes = [ctypes.c_int, ctypes.POINTER(Component), ctypes.c_double,
@@ -269,6 +288,94 @@ class Lattice:
     def restore(self, buf, t):
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         self._check(lib().lbm_restore(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.size, int(t)))
+
+
+class Batch:
+    """Many independent D2Q9 lattices behind lbm_batch_create. `cases` is a list of dicts with
+    keys shape (nx, ny), components [(Tc, pc, omega, M)], T, tau and optional gamma, kij,
+    beta, G, mrt_rates, rho_ref; collision and precision are common to all cases."""
+
+    def __init__(self, cases, collision=BGK, precision=FP64):
+        L = lib()
+        n = len(cases)
+        nc = len(cases[0]["components"])
+        self.nc = nc
+        self.shapes = [tuple(int(v) for v in c["shape"]) for c in cases]
+        self.sizes = [s[0] * s[1] for s in self.shapes]
+        grids = (Grid * n)()
+        comps = (Component * (n * nc))()
+        eoss = (Eos * n)()
+        taus = np.array([float(c["tau"]) for c in cases])
+        self._keep = [taus]
+        for i, c in enumerate(cases):
+            g, cp, e, keep = make_args(c["shape"], c["components"], c["T"], gamma=c.get("gamma"),
+                                       kij=c.get("kij"), beta=c.get("beta", 1.0), G=c.get("G", -1.0),
+                                       collision=collision, mrt_rates=c.get("mrt_rates"),
+                                       precision=precision, rho_ref=c.get("rho_ref"))
+            grids[i] = g
+            for k in range(nc):
+                comps[i * nc + k] = cp[k]
+            eoss[i] = e
+            self._keep.append(keep)
+        h = ctypes.c_void_p()
+        st = L.lbm_batch_create(n, grids, nc, comps, eoss, _dp(taus), ctypes.byref(h))
+        if st != OK:
+            raise LBMError(st, L.lbm_batch_last_error(None).decode())
+        self._h = h
+        self.ncase = n
+
+    def _check(self, st):
+        if st != OK:
+            raise LBMError(st, lib().lbm_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, rho_list):
+        """rho_list[i]: array (nc, ny, nx) of case i."""
+        flat = np.concatenate([np.ascontiguousarray(r, dtype=np.float64).ravel() for r in rho_list])
+        self._check(lib().lbm_batch_init(self._h, _dp(flat), None))
+
+    def step(self, n):
+        self._check(lib().lbm_batch_step(self._h, int(n)))
+
+    def tune(self, trial_steps=20):
+        self._check(lib().lbm_batch_tune(self._h, int(trial_steps)))
+        return lib().lbm_batch_tune_report(self._h).decode()
+
+    def case_status(self):
+        st = (ctypes.c_int * self.ncase)()
+        t = (ctypes.c_int64 * self.ncase)()
+        self._check(lib().lbm_batch_case_status(self._h, st, t))
+        return list(st), list(t)
+
+    def rho(self):
+        """List of (nc, ny, nx) density arrays, one per case."""
+        total = sum(self.sizes) * self.nc
+        out = np.empty(total)
+        self._check(lib().lbm_batch_fields(self._h, _dp(out), None, None))
+        res, off = [], 0
+        for (nx, ny), n in zip(self.shapes, self.sizes):
+            res.append(out[off:off + self.nc * n].reshape(self.nc, ny, nx))
+            off += self.nc * n
+        return res
+
+    def rho_into(self, out):
+        self._check(lib().lbm_batch_fields(self._h, _dp(out), None, None))
+
+    def get_f(self, i):
+        nx, ny = self.shapes[i]
+        f = np.empty((self.nc, 9, ny, nx))
+        self._check(lib().lbm_batch_get_f(self._h, int(i), _dp(f)))
+        return f
 
 
 def scale_to_lattice(components, T_phys, p_phys):

@@ -1,0 +1,140 @@
+"""The batched path (many independent D2Q9 cases, one block per case kept in shared memory,
+one launch per size class, graph-replayed chunks) against single-lattice contexts (bit for
+bit: the same per-site code) and the FP64 oracle, and its autotuner."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import lbm_inputs
+import oracle
+from conftest import GOLDEN
+from lbm_cases import comps_of, initial_rho, oracle_case
+
+pytestmark = pytest.mark.gpu
+
+FP64, FP32S = 0, 1
+
+
+@pytest.fixture(scope="module")
+def sweep():
+    with open(os.path.join(GOLDEN, "cases.json")) as fh:
+        return json.load(fh)["c4"]
+
+
+def _batch_case(sweep, c):
+    return dict(shape=c["shape"], components=comps_of(c), T=c["T"], tau=sweep["tau"], gamma=c["gamma"],
+                kij=np.array(c["kij"]), beta=sweep["beta"], G=c["G"])
+
+
+def _pick(sweep, n, seed=3):
+    """n cases of different widths from the sweep."""
+    out, seen = [], set()
+    for c in sweep["cases"]:
+        if c["shape"][0] not in seen:
+            out.append(c)
+            seen.add(c["shape"][0])
+        if len(out) == n:
+            break
+    return out
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32S])
+def test_batch_equals_single_contexts_bitwise(sweep, precision):
+    from paper_1909_12390_gb300 import lbm
+    picked = _pick(sweep, 5)
+    rhos = [initial_rho(c, tuple(c["shape"])) for c in picked]
+    b = lbm.Batch([_batch_case(sweep, c) for c in picked], precision=precision)
+    b.init(rhos)
+    b.step(130)  # one graph-replayed chunk of 100 and a direct launch of 30
+    st, t = b.case_status()
+    assert st == [0] * len(picked) and t == [130] * len(picked)
+    for i, (c, rho) in enumerate(zip(picked, rhos)):
+        one = lbm.Lattice(tuple(c["shape"]), comps_of(c), T=c["T"], tau=sweep["tau"], gamma=c["gamma"],
+                          kij=np.array(c["kij"]), beta=sweep["beta"], G=c["G"], precision=precision)
+        one.set_path(lbm.PATH_TWO_KERNEL)
+        one.init(rho)
+        one.step(130)
+        assert np.array_equal(b.get_f(i), one.get_f()), i
+        one.close()
+    b.close()
+
+
+def test_batch_cases_match_oracle(sweep):
+    from paper_1909_12390_gb300 import lbm
+    picked = _pick(sweep, 3)
+    rhos = [initial_rho(c, tuple(c["shape"])) for c in picked]
+    b = lbm.Batch([_batch_case(sweep, c) for c in picked], precision=FP32S)
+    b.init(rhos)
+    b.step(300)
+    got = b.rho()
+    for c, rho, g in zip(picked, rhos, got):
+        oc = dict(c, tau=sweep["tau"], beta=sweep["beta"], Q=9)
+        ocase = oracle_case(oc, tuple(c["shape"]), collision=0)
+        want = oracle.fields(ocase, oracle.step(ocase, oracle.equilibrium(ocase, rho), 300)).rho
+        assert float(np.max(np.abs(g - want) / want.sum(0))) < 2e-4
+
+
+def test_batch_tune_keeps_state_and_reports(sweep):
+    from paper_1909_12390_gb300 import lbm
+    picked = _pick(sweep, 5)
+    rhos = [initial_rho(c, tuple(c["shape"])) for c in picked]
+    b = lbm.Batch([_batch_case(sweep, c) for c in picked], precision=FP32S)
+    b.init(rhos)
+    b.step(10)
+    before = [b.get_f(i) for i in range(len(picked))]
+    rep = b.tune(10)
+    assert rep.count("threads=") == len({tuple(c["shape"]) for c in picked})
+    after = [b.get_f(i) for i in range(len(picked))]
+    for x, y in zip(before, after):
+        assert np.array_equal(x, y)
+    assert b.case_status()[1] == [10] * len(picked)
+
+
+def test_batch_failing_case_is_isolated(sweep):
+    """One case with G > 0 (psi^2 < 0) stops at its first step; the others run on."""
+    from paper_1909_12390_gb300 import lbm
+    picked = _pick(sweep, 3)
+    specs = [_batch_case(sweep, c) for c in picked]
+    specs[1] = dict(specs[1], G=1.0)
+    b = lbm.Batch(specs, precision=FP32S)
+    b.init([initial_rho(c, tuple(c["shape"])) for c in picked])
+    with pytest.raises(lbm.LBMError) as ei:
+        b.step(20)
+    assert ei.value.status == lbm.ERR_PSI_DOMAIN
+    st, t = b.case_status()
+    assert st[1] == lbm.ERR_PSI_DOMAIN and t[1] == 0
+    assert st[0] == 0 and st[2] == 0 and t[0] == 20 and t[2] == 20
+
+
+def test_full_sweep_runs_and_matches_flash(sweep):
+    """All 512 cases for the full 10000 steps in FP32-shifted storage: every case completes;
+    sampled cases reach bulk compositions within the paper's reported accuracy of the flash
+    (4.0 % composition, Section 4.2) and match the oracle run of the same case."""
+    from paper_1909_12390_gb300 import lbm
+    cs = sweep["cases"]
+    b = lbm.Batch([_batch_case(sweep, c) for c in cs], precision=FP32S)
+    rhos = [initial_rho(c, tuple(c["shape"])) for c in cs]
+    b.init(rhos)
+    b.tune(20)
+    b.step(sweep["steps"])
+    st, t = b.case_status()
+    assert all(s == 0 for s in st) and all(x == sweep["steps"] for x in t)
+    got = b.rho()
+    worst = 0.0
+    for i in (0, 137, 411):
+        c = cs[i]
+        nx = c["shape"][0]
+        r = got[i]
+        n = r / np.array([d["M"] for d in c["components"]])[:, None, None]
+        liq = n[:, :, nx // 2 - 4:nx // 2 + 4].mean(axis=(1, 2))
+        vap = np.concatenate([n[:, :, :4], n[:, :, -4:]], axis=2).mean(axis=(1, 2))
+        x1, y1 = liq[0] / liq.sum(), vap[0] / vap.sum()
+        assert abs(x1 / c["x"][0] - 1) < 0.04 and abs(y1 / c["y"][0] - 1) < 0.04
+        oc = dict(c, tau=sweep["tau"], beta=sweep["beta"], Q=9)
+        ocase = oracle_case(oc, tuple(c["shape"]), collision=0)
+        want = oracle.fields(ocase, oracle.step(ocase, oracle.equilibrium(ocase, rhos[i]), sweep["steps"])).rho
+        worst = max(worst, float(np.max(np.abs(r - want) / want.sum(0))))
+    print("batched sweep sampled cases: max error vs oracle %.3e" % worst)
+    assert worst < 2e-4

@@ -33,8 +33,11 @@ def _pair(c, shape, precision, collision, rates):
     return a, b
 
 
-# grids that tile: D3Q19 tiles are 32 x 8 (x, y), D2Q9 tiles are 128 (x); chunks of >= 4 planes
-@pytest.mark.parametrize("shape", [(32, 8, 8), (64, 16, 12), (128, 8), (256, 12)])
+# grids that tile: D3Q19 tiles are 32 x 8 (x, y), D2Q9 tiles are 128 (x); the marched axis
+# is cut into chunks of at least two groups of 4 planes: (32, 8, 8) and (128, 8) are one chunk,
+# (64, 16, 16) two, (32, 16, 24) three, (256, 24) three, (128, 64) eight
+@pytest.mark.parametrize("shape", [(32, 8, 8), (64, 16, 12), (64, 16, 16), (32, 16, 24), (128, 8), (256, 12),
+                                   (256, 24), (128, 64)])
 @pytest.mark.parametrize("precision", [FP64, FP32S])
 @pytest.mark.parametrize("collision", [0, 1])
 def test_fused_equals_two_kernel_bitwise(cases, shape, precision, collision):
