@@ -58,7 +58,7 @@ enum { LBM_BGK = 0, LBM_MRT = 1 };
 enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1 };
 
 typedef struct {
-  int nx, ny, nz; /* sites per axis, periodic; nz = 1 for D2Q9 */
+  int nx, ny, nz; /* sites per axis, periodic; nz = 1 for D2Q9; Q * nx * ny * nz < 2^32 */
   int lattice;    /* LBM_D2Q9 or LBM_D3Q19 */
 } lbm_grid;
 
@@ -171,6 +171,22 @@ lbm_status lbm_test_silence_block(lbm_ctx *ctx, int block);
  * the stream. */
 lbm_status lbm_profile(lbm_ctx *ctx, int on);
 lbm_status lbm_profile_read(lbm_ctx *ctx, int kernel, double *total_ms, int64_t *launches);
+
+/* ---- Adjoint (gradients; BGK collision) ----------------------------------------------
+ * lbm_record advances n steps from the current state like lbm_step and keeps a copy of the
+ * raw state every checkpoint_every steps (the first at the current step). lbm_adjoint then
+ * back-propagates dL/drho of the final state (host array drho[nc][N], the loss gradient with
+ * respect to the cell-volume densities the recorded run ended with) through every recorded step
+ * with the hand-written discrete adjoint of the step (collision with Guo forcing, split of
+ * Eq. distributionforce, force of Eq. coupledMCforce, EOS of Eq. MCPengRobinson),
+ * recomputing each segment's states from its checkpoint. Outputs (any may be NULL):
+ * dkij[nc*nc] = dL/dzeta_ij per matrix entry (for a symmetric coefficient add the (i,j) and
+ * (j,i) entries), dgamma[nc] = dL/dgamma_i, drho0[nc][N] = dL/drho at the recorded start for
+ * an equilibrium start at rest (lbm_init with u = NULL). Arithmetic in the storage precision
+ * (FP32 for LBM_FP32_SHIFTED) with the EOS derivative and the reductions in FP64. Device
+ * memory: checkpoint_every states plus four adjoint fields, allocated for the call. */
+lbm_status lbm_record(lbm_ctx *ctx, int64_t n, int checkpoint_every);
+lbm_status lbm_adjoint(lbm_ctx *ctx, const double *drho, double *dkij, double *dgamma, double *drho0);
 
 /* ---- Batched lattices -------------------------------------------------------------------
  * Many small independent D2Q9 cases (each its own grid, components' constants, temperature,

@@ -1,0 +1,353 @@
+// Hand-written discrete adjoint of the BGK step (Eq. LBE with the Guo forcing of Eq.
+// equilibrium, the split of Eq. distributionforce, the force of Eq. coupledMCforce and the EOS
+// of Eq. MCPengRobinson), for gradients of a loss on the final cell-volume densities with
+// respect to the binary interaction coefficients zeta_ij, the volatility coefficients gamma_i
+// and the initial densities.
+//
+// Forward, per site x (t -> t + 1): rho_s = sum_a f_sa, j = sum e_a f_sa, psi(rho), F from the
+// psi stencil, chi_s = gamma_s rho_s / Gam, u = (j + F/2)/rho,
+//   f*_sa = (1 - w) f_sa + w feq_sa(rho_s, u) + gk chi_s Fb_a(u, F),  f_sa(x + e_a) = f*_sa(x).
+// Reverse, given lam(t+1) = dL/df(t+1) (canonical layout):
+//   lam*_sa(x) = lam_sa(x + e_a)                                          (un-stream)
+//   with L0_s = sum_a w_a lam*_sa, L1_s = sum_a w_a lam*_sa e_a, L2_s = sum_a w_a lam*_sa e_a e_a:
+//   ubar   = sum_s w rho_s (3 L1 + 9 L2 u - 3 u L0) + gk chi_s (-3 F L0 + 9 L2 F)
+//   Fbar   = gk sum_s chi_s (3 L1 - 3 u L0 + 9 L2 u) + ubar / (2 rho)
+//   chibar = gk (3 L1.F - 3 (u.F) L0 + 9 u.L2.F)
+//   rbar_s = w (L0 + 3 L1.u + 9/2 u.L2.u - 3/2 u.u L0) - ubar.u / rho
+//            + gamma_s (chibar_s - sum_k chibar_k chi_k) / Gam            (pass A)
+//   psibar(y) = c1 Fbar(y).S1(y) + sum_a w_a e_a.Fbar(y - e_a) [c1 psi(y - e_a) + 2 c2 psi(y)]
+//   rbar_s += (psibar / 2 psi) cpsi (dp/dn_s / M_s - 1/3)                  (pass B)
+//   lam_sa(t) = (1 - w) lam*_sa + rbar_s + (ubar / rho).e_a
+// Parameter gradients: dL/dgamma_k = sum_x rho_k (chibar_k - sum chibar chi) / Gam and
+// dL/dzeta_ij = sum_x pbar n_i n_j sqrt(a_i alpha_i a_j alpha_j) / (1 + 2B - B^2), reduced in
+// FP64 per block and summed on the host in a fixed order.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_host.h"
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+constexpr int kAdjBlock = 256;
+
+template <int Q, int NC, class Prec, int PAR>
+__device__ __forceinline__ void load_site(const Params& P, const typename Prec::S* __restrict__ f, const Site& s,
+                                          typename Prec::R (&rc)[NC], typename Prec::R (&j)[3]) {
+  using R = typename Prec::R;
+  using L = Lat<Q>;
+  j[0] = j[1] = j[2] = 0;
+  For<0, NC>::run([&]<int C>() {
+    const typename Prec::S* fc = comp_base<Q>(f, P, C);
+    R acc = 0;
+    For<0, Q>::run([&]<int A>() {
+      const R v = (R)fc[AA<Q>::template rd<A, PAR>(P, s)];
+      acc += v;
+#pragma unroll
+      for (int d = 0; d < L::D; ++d) {
+        if (L::e(A, d) > 0) j[d] += v;
+        if (L::e(A, d) < 0) j[d] -= v;
+      }
+    });
+    rc[C] = PC<R>::rho_ref(P, C) + acc;
+  });
+}
+
+// Pass A: collision adjoint at every site x. Writes Fbar (D), jbar = ubar / rho (D) and the
+// partial rbar (NC) per site, and the per-block partial sums of dL/dgamma.
+template <int Q, int NC, class Prec, int PAR>
+__global__ void __launch_bounds__(kAdjBlock) k_adj_a(const Params P, const typename Prec::S* __restrict__ f,
+                                                     const typename Prec::PsiT* __restrict__ psi,
+                                                     const typename Prec::R* __restrict__ lam, typename Prec::R* Fbar,
+                                                     typename Prec::R* jbar, typename Prec::R* rbar,
+                                                     double* gpart) {
+  using R = typename Prec::R;
+  using L = Lat<Q>;
+  constexpr int D = L::D;
+  __shared__ double red[kAdjBlock];
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double gg[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) gg[c] = 0;
+  if (idx < P.N) {
+    Site s;
+    s.set(P, (uint32_t)idx);
+    R rc[NC], j[3];
+    load_site<Q, NC, Prec, PAR>(P, f, s, rc, j);
+    // forward force
+    R s1[3] = {0, 0, 0}, s2[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 1; a < Q; ++a) {
+      const R pn = (R)psi[s.nb(P, L::e(a, 0), L::e(a, 1), L::e(a, 2))];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        s1[d] += (R)L::w(a) * pn * (R)L::e(a, d);
+        s2[d] += (R)L::w(a) * pn * pn * (R)L::e(a, d);
+      }
+    }
+    const R p0 = (R)psi[idx];
+    R F[3] = {0, 0, 0}, u[3] = {0, 0, 0};
+    R rho = 0, gs = 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      rho += rc[c];
+      gs += PC<R>::gamma(P, c) * rc[c];
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      F[d] = PC<R>::c1(P) * p0 * s1[d] + PC<R>::c2(P) * s2[d];
+      u[d] = (j[d] + (R)0.5 * F[d]) / rho;
+    }
+    R uu = 0, uF = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      uu += u[d] * u[d];
+      uF += u[d] * F[d];
+    }
+    const R om = PC<R>::omega(P), gk = PC<R>::gk(P);
+    R ub[3] = {0, 0, 0}, Fd[3] = {0, 0, 0}, chib[NC], rb[NC], chi[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      chi[c] = PC<R>::gamma(P, c) * rc[c] / gs;
+      R L0 = 0, L1[3] = {0, 0, 0}, L2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        const R lw = (R)L::w(a) * lam[((int64_t)c * Q + a) * P.N + s.nb(P, L::e(a, 0), L::e(a, 1), L::e(a, 2))];
+        L0 += lw;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          L1[d] += lw * (R)L::e(a, d);
+#pragma unroll
+          for (int e2 = 0; e2 < D; ++e2) L2[d][e2] += lw * (R)(L::e(a, d) * L::e(a, e2));
+        }
+      }
+      R L2u[3] = {0, 0, 0}, L2F[3] = {0, 0, 0};
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+#pragma unroll
+        for (int e2 = 0; e2 < D; ++e2) {
+          L2u[d] += L2[d][e2] * u[e2];
+          L2F[d] += L2[d][e2] * F[e2];
+        }
+      R L1u = 0, L1F = 0, uL2u = 0, uL2F = 0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        L1u += L1[d] * u[d];
+        L1F += L1[d] * F[d];
+        uL2u += u[d] * L2u[d];
+        uL2F += u[d] * L2F[d];
+      }
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        ub[d] += om * rc[c] * ((R)3 * L1[d] + (R)9 * L2u[d] - (R)3 * u[d] * L0) +
+                 gk * chi[c] * ((R)-3 * F[d] * L0 + (R)9 * L2F[d]);
+        Fd[d] += gk * chi[c] * ((R)3 * L1[d] - (R)3 * u[d] * L0 + (R)9 * L2u[d]);
+      }
+      chib[c] = gk * ((R)3 * L1F - (R)3 * uF * L0 + (R)9 * uL2F);
+      rb[c] = om * (L0 + (R)3 * L1u + (R)4.5 * uL2u - (R)1.5 * uu * L0);
+    }
+    R ubu = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) ubu += ub[d] * u[d];
+    R cc = 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) cc += chib[c] * chi[c];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      rb[c] += -ubu / rho + PC<R>::gamma(P, c) * (chib[c] - cc) / gs;
+      gg[c] = (double)(rc[c] * (chib[c] - cc) / gs);
+      rbar[c * P.N + idx] = rb[c];
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      Fbar[d * P.N + idx] = Fd[d] + ub[d] / ((R)2 * rho);
+      jbar[d * P.N + idx] = ub[d] / rho;
+    }
+  }
+  // per-block partial sums of dL/dgamma, fixed order
+  for (int c = 0; c < NC; ++c) {
+    red[threadIdx.x] = gg[c];
+    __syncthreads();
+    for (int st = kAdjBlock / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) gpart[(int64_t)blockIdx.x * NC + c] += red[0];
+    __syncthreads();
+  }
+}
+
+// Pass B: force / pseudo-potential / EOS adjoint and the new lam(t). kpart receives the
+// per-block partial sums of dL/dzeta_ij (NC x NC).
+template <int Q, int NC, class Prec, int PAR>
+__global__ void __launch_bounds__(kAdjBlock) k_adj_b(const Params P, const typename Prec::S* __restrict__ f,
+                                                     const typename Prec::PsiT* __restrict__ psi,
+                                                     const typename Prec::R* __restrict__ lam,
+                                                     const typename Prec::R* __restrict__ Fbar,
+                                                     const typename Prec::R* __restrict__ jbar,
+                                                     const typename Prec::R* __restrict__ rbar,
+                                                     typename Prec::R* lam_out, double* kpart) {
+  using R = typename Prec::R;
+  using L = Lat<Q>;
+  constexpr int D = L::D;
+  __shared__ double red[kAdjBlock];
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double kg[NC * NC];
+#pragma unroll
+  for (int k = 0; k < NC * NC; ++k) kg[k] = 0;
+  if (idx < P.N) {
+    Site s;
+    s.set(P, (uint32_t)idx);
+    R rc[NC], j[3];
+    load_site<Q, NC, Prec, PAR>(P, f, s, rc, j);
+    const R p0 = (R)psi[idx];
+    // psibar(y) = c1 Fbar(y).S1(y) + sum_a w_a e_a.Fbar(y - e_a) [c1 psi(y - e_a) + 2 c2 psi(y)]
+    R pb = 0;
+    R S1[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 1; a < Q; ++a) {
+      const int64_t yp = s.nb(P, L::e(a, 0), L::e(a, 1), L::e(a, 2));
+      const int64_t ym = s.nb(P, -L::e(a, 0), -L::e(a, 1), -L::e(a, 2));
+      const R pp = (R)psi[yp], pm = (R)psi[ym];
+      R eFm = 0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        S1[d] += (R)L::w(a) * pp * (R)L::e(a, d);
+        eFm += (R)L::e(a, d) * Fbar[d * P.N + ym];
+      }
+      pb += (R)L::w(a) * eFm * (PC<R>::c1(P) * pm + (R)2 * PC<R>::c2(P) * p0);
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) pb += PC<R>::c1(P) * Fbar[d * P.N + idx] * S1[d];
+    // psi = sqrt(psi2), psi2 = cpsi (p - rho / 3): the EOS derivative in FP64
+    const double psi2b = (double)pb / (2.0 * (double)p0);
+    const double pbar = P.cpsi * psi2b;
+    double n[NC], nt = 0, B = 0, A2 = 0, An[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      n[i] = (double)rc[i] * P.invM[i];
+      nt += n[i];
+      B += P.b[i] * n[i];
+    }
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      An[i] = 0;
+#pragma unroll
+      for (int k = 0; k < NC; ++k) An[i] += P.Qa[i * 4 + k] * n[k];
+      A2 += n[i] * An[i];
+    }
+    const double d1 = 1.0 - B, d2 = 1.0 + 2.0 * B - B * B;
+    R rb[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      const double dpdn = P.RT / d1 + nt * P.RT * P.b[i] / (d1 * d1) - 2.0 * An[i] / d2 +
+                          A2 * (2.0 - 2.0 * B) * P.b[i] / (d2 * d2);
+      rb[i] = rbar[i * P.N + idx] + (R)(pbar * dpdn * P.invM[i] - P.cpsi * psi2b / 3.0);
+#pragma unroll
+      for (int k = 0; k < NC; ++k) kg[i * NC + k] = pbar * n[i] * n[k] * P.sa[i] * P.sa[k] / d2;
+    }
+    R jb[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < D; ++d) jb[d] = jbar[d * P.N + idx];
+    const R w1 = (R)1 - PC<R>::omega(P);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        R v = w1 * lam[((int64_t)c * Q + a) * P.N + s.nb(P, L::e(a, 0), L::e(a, 1), L::e(a, 2))] + rb[c];
+#pragma unroll
+        for (int d = 0; d < D; ++d) v += jb[d] * (R)L::e(a, d);
+        lam_out[((int64_t)c * Q + a) * P.N + idx] = v;
+      }
+  }
+  for (int k = 0; k < NC * NC; ++k) {
+    red[threadIdx.x] = kg[k];
+    __syncthreads();
+    for (int st = kAdjBlock / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) kpart[(int64_t)blockIdx.x * NC * NC + k] += red[0];
+    __syncthreads();
+  }
+}
+
+// lam(T)_sa(x) = dL/drho_s(x) for every a; dL/drho(0)_s(x) = sum_a w_a lam(0)_sa(x).
+template <int Q, int NC, class Prec>
+__global__ void k_adj_seed(const Params P, const double* __restrict__ drho, typename Prec::R* lam) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P.N) return;
+  for (int c = 0; c < NC; ++c)
+    for (int a = 0; a < Q; ++a) lam[((int64_t)c * Q + a) * P.N + idx] = (typename Prec::R)drho[c * P.N + idx];
+}
+
+template <int Q, int NC, class Prec>
+__global__ void k_adj_init_grad(const Params P, const typename Prec::R* __restrict__ lam, double* drho0) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P.N) return;
+  for (int c = 0; c < NC; ++c) {
+    double acc = 0;
+    for (int a = 0; a < Q; ++a) acc += Lat<Q>::w(a) * (double)lam[((int64_t)c * Q + a) * P.N + idx];
+    drho0[c * P.N + idx] = acc;
+  }
+}
+
+struct AdjFns {  // same layout as the declaration in lbm_capi.cu
+  void (*seed)(const Params&, const double*, void*, cudaStream_t);
+  void (*pass_a)(const Params&, const void* f, const void* psi, const void* lam, void* Fb, void* jb, void* rb,
+                 int parity, double* gpart, cudaStream_t);
+  void (*pass_b)(const Params&, const void* f, const void* psi, const void* lam, const void* Fb, const void* jb,
+                 const void* rb, void* lam_out, int parity, double* kpart, cudaStream_t);
+  void (*init_grad)(const Params&, const void* lam, double* drho0, cudaStream_t);
+  int real_bytes;
+};
+
+template <int Q, int NC, class Prec>
+struct AdjLaunch {
+  using R = typename Prec::R;
+  using S = typename Prec::S;
+  using PsiT = typename Prec::PsiT;
+  static unsigned blocks(const Params& P) { return (unsigned)((P.N + kAdjBlock - 1) / kAdjBlock); }
+  static void seed(const Params& P, const double* d, void* lam, cudaStream_t s) {
+    k_adj_seed<Q, NC, Prec><<<blocks(P), kAdjBlock, 0, s>>>(P, d, (R*)lam);
+  }
+  static void pass_a(const Params& P, const void* f, const void* psi, const void* lam, void* Fb, void* jb, void* rb,
+                     int parity, double* gp, cudaStream_t s) {
+    auto k = parity ? k_adj_a<Q, NC, Prec, 1> : k_adj_a<Q, NC, Prec, 0>;
+    k<<<blocks(P), kAdjBlock, 0, s>>>(P, (const S*)f, (const PsiT*)psi, (const R*)lam, (R*)Fb, (R*)jb, (R*)rb, gp);
+  }
+  static void pass_b(const Params& P, const void* f, const void* psi, const void* lam, const void* Fb,
+                     const void* jb, const void* rb, void* lo, int parity, double* kp, cudaStream_t s) {
+    auto k = parity ? k_adj_b<Q, NC, Prec, 1> : k_adj_b<Q, NC, Prec, 0>;
+    k<<<blocks(P), kAdjBlock, 0, s>>>(P, (const S*)f, (const PsiT*)psi, (const R*)lam, (const R*)Fb, (const R*)jb,
+                                      (const R*)rb, (R*)lo, kp);
+  }
+  static void init_grad(const Params& P, const void* lam, double* d, cudaStream_t s) {
+    k_adj_init_grad<Q, NC, Prec><<<blocks(P), kAdjBlock, 0, s>>>(P, (const R*)lam, d);
+  }
+  static const AdjFns* table() {
+    static const AdjFns t = {seed, pass_a, pass_b, init_grad, (int)sizeof(R)};
+    return &t;
+  }
+};
+
+template <int Q, class Prec>
+const AdjFns* adj_nc(int nc) {
+  switch (nc) {
+    case 1: return AdjLaunch<Q, 1, Prec>::table();
+    case 2: return AdjLaunch<Q, 2, Prec>::table();
+    case 3: return AdjLaunch<Q, 3, Prec>::table();
+    case 4: return AdjLaunch<Q, 4, Prec>::table();
+  }
+  return nullptr;
+}
+
+const AdjFns* adj_fns(int Q, int nc, int precision) {
+  if (Q == 9) return precision == LBM_FP64 ? adj_nc<9, PrecF64>(nc) : adj_nc<9, PrecF32S>(nc);
+  return precision == LBM_FP64 ? adj_nc<19, PrecF64>(nc) : adj_nc<19, PrecF32S>(nc);
+}
+
+}  // namespace lbm

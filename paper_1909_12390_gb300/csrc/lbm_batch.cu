@@ -28,13 +28,41 @@ struct BatchCase {
   int64_t site_off;  // site offset of the case (pseudo-potential buffer, fields)
 };
 
+// One step of one case held by this block: psi of every site, barrier, collide and stream.
+// Returns the status bits of the psi pass (uniform over the block).
+template <int Q, int NC, class Prec, int MRT, int PAR>
+__device__ __forceinline__ int batch_step(const Params& P, typename Prec::S* f, typename Prec::PsiT* psi) {
+  using R = typename Prec::R;
+  using L = Lat<Q>;
+  const uint32_t N = P.N32;
+  int err = 0;
+  for (uint32_t idx = threadIdx.x; idx < N; idx += blockDim.x) {
+    Site s;
+    s.set(P, idx);
+    typename Prec::PsiT v;
+    err |= site_psi<Q, NC, Prec, PAR>(P, f, s, v);
+    psi[idx] = v;
+  }
+  err = __syncthreads_or(err);
+  if (err) return err;
+  for (uint32_t idx = threadIdx.x; idx < N; idx += blockDim.x) {
+    Site s;
+    s.set(P, idx);
+    R pn[Q];
+    pn[0] = (R)psi[idx];
+#pragma unroll
+    for (int a = 1; a < Q; ++a) pn[a] = (R)psi[s.nb(P, L::e(a, 0), L::e(a, 1), L::e(a, 2))];
+    site_collide<Q, NC, Prec, MRT, PAR>(P, f, s, pn);
+  }
+  __syncthreads();
+  return 0;
+}
+
 template <int Q, int NC, class Prec, int MRT>
 __global__ void k_batch(const BatchCase* __restrict__ cases, const int* __restrict__ order, typename Prec::S* f_all,
                         typename Prec::PsiT* psi_all, int* case_status, long long* case_t, int nsteps, int use_smem) {
   using S = typename Prec::S;
   using PsiT = typename Prec::PsiT;
-  using R = typename Prec::R;
-  using L = Lat<Q>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Params P;
   __shared__ int64_t foff, soff;
@@ -57,30 +85,12 @@ __global__ void k_batch(const BatchCase* __restrict__ cases, const int* __restri
   int st = case_status[ci];
   int done = 0;
   for (int k = 0; k < nsteps && st == 0; ++k) {
-    const int parity = (int)((t0 + k) & 1);
-    int err = 0;
-    for (int64_t idx = threadIdx.x; idx < N; idx += blockDim.x) {
-      Site s;
-      s.set(P, idx);
-      PsiT v;
-      err |= site_psi<Q, NC, Prec>(P, f, s, idx, parity, v);
-      psi[idx] = v;
-    }
-    err = __syncthreads_or(err);
+    const int err = ((t0 + k) & 1) ? batch_step<Q, NC, Prec, MRT, 1>(P, f, psi)
+                                   : batch_step<Q, NC, Prec, MRT, 0>(P, f, psi);
     if (err) {
       st = err;
       break;
     }
-    for (int64_t idx = threadIdx.x; idx < N; idx += blockDim.x) {
-      Site s;
-      s.set(P, idx);
-      R pn[Q];
-      pn[0] = (R)psi[idx];
-#pragma unroll
-      for (int a = 1; a < Q; ++a) pn[a] = (R)psi[s.nb(P, L::e(a, 0), L::e(a, 1), L::e(a, 2))];
-      site_collide<Q, NC, Prec, MRT>(P, f, s, idx, parity, pn);
-    }
-    __syncthreads();
     ++done;
   }
   if (use_smem)

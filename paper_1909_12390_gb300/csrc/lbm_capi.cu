@@ -3,6 +3,7 @@
 // captured CUDA graph once it is long enough) and read-back.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -74,8 +75,25 @@ struct lbm_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, int>> ev_marks[3];  // (start, stop) pool indices per kernel kind
   size_t ev_used = 0;
+  // adjoint recording (lbm_record): checkpoints of the raw storage every ck_every steps
+  std::vector<void*> ckpt;
+  int ck_every = 0;
+  int64_t rec_t0 = -1, rec_n = 0;
   std::string err;
 };
+
+namespace lbm {
+struct AdjFns {
+  void (*seed)(const Params&, const double*, void*, cudaStream_t);
+  void (*pass_a)(const Params&, const void* f, const void* psi, const void* lam, void* Fb, void* jb, void* rb,
+                 int parity, double* gpart, cudaStream_t);
+  void (*pass_b)(const Params&, const void* f, const void* psi, const void* lam, const void* Fb, const void* jb,
+                 const void* rb, void* lam_out, int parity, double* kpart, cudaStream_t);
+  void (*init_grad)(const Params&, const void* lam, double* drho0, cudaStream_t);
+  int real_bytes;
+};
+const AdjFns* adj_fns(int Q, int nc, int precision);
+}  // namespace lbm
 
 namespace {
 
@@ -293,7 +311,8 @@ lbm_status make_params(const lbm_grid* grid, int nc, const lbm_component* comps,
   if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return bad("grid sizes must be >= 1");
   if (grid->lattice == LBM_D2Q9 && grid->nz != 1) return bad("D2Q9 needs nz == 1");
   const int64_t N = (int64_t)grid->nx * grid->ny * grid->nz;
-  if (N > ((int64_t)1 << 40)) return bad("grid too large");
+  if (N * grid->lattice >= ((int64_t)1 << 32))
+    return bad("grid too large: Q * nx * ny * nz must stay below 2^32 (226 M D3Q19 sites)");
   if (nc < 1 || nc > 4) return bad("nc must be 1..4");
   if (!(tau > 0.5) || !std::isfinite(tau)) return bad("tau must be > 1/2");
   if (eos->precision != LBM_FP64 && eos->precision != LBM_FP32_SHIFTED)
@@ -325,9 +344,7 @@ lbm_status make_params(const lbm_grid* grid, int nc, const lbm_component* comps,
     for (int k = 0; k < Q; ++k)
       if (!std::isfinite(eos->mrt_rates[k]) || !(eos->mrt_rates[k] > 0) || !(eos->mrt_rates[k] < 2))
         return bad("mrt_rates[%d] must lie in (0, 2)", k);
-  const bool f64 = eos->precision == LBM_FP64;
-  const Ops* ops = Q == 9 ? (f64 ? ops_q9_f64 : ops_q9_f32s)(nc, eos->collision)
-                               : (f64 ? ops_q19_f64 : ops_q19_f32s)(nc, eos->collision);
+  const Ops* ops = ops_get(Q, eos->precision == LBM_FP32_SHIFTED, eos->collision == LBM_MRT, nc);
   if (!ops) return bad("no kernels for this configuration");
 
   Params& P = *out;
@@ -336,6 +353,7 @@ lbm_status make_params(const lbm_grid* grid, int nc, const lbm_component* comps,
   P.ny = grid->ny;
   P.nz = grid->nz;
   P.N = N;
+  P.N32 = (uint32_t)N;
   P.nc = nc;
   P.omega = 1.0 / tau;
   for (int i = 0; i < nk_q(Q); ++i) {
@@ -425,6 +443,7 @@ void lbm_destroy(lbm_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_graph(c);
   free_fused(c);
+  for (void* p : c->ckpt) cudaFree(p);
   cudaFree(c->f);
   cudaFree(c->psi);
   cudaFree(c->status);
@@ -660,6 +679,132 @@ lbm_status lbm_restore(lbm_ctx* c, const void* buf, size_t bytes, int64_t t) {
   CK(c, reset_fused_flags(c));
   CK(c, cudaStreamSynchronize(c->stream));
   c->t = t;
+  return LBM_OK;
+}
+
+lbm_status lbm_record(lbm_ctx* c, int64_t n, int checkpoint_every) {
+  if (!c) return LBM_ERR_ARG;
+  if (c->collision != LBM_BGK) return fail(c, LBM_ERR_ARG, "the adjoint covers the BGK collision only");
+  if (n < 1 || checkpoint_every < 1) return fail(c, LBM_ERR_ARG, "n and checkpoint_every must be >= 1");
+  for (void* p : c->ckpt) cudaFree(p);
+  c->ckpt.clear();
+  c->rec_t0 = -1;
+  const size_t bytes = lbm_state_bytes(c);
+  const int64_t t0 = c->t;
+  for (int64_t done = 0; done < n;) {
+    void* p = nullptr;
+    CK(c, cudaMalloc(&p, bytes));
+    c->ckpt.push_back(p);
+    CK(c, cudaMemcpyAsync(p, c->f, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    const int64_t k = std::min<int64_t>(checkpoint_every, n - done);
+    lbm_status st = lbm_step(c, k);
+    if (st != LBM_OK) return st;
+    done += k;
+  }
+  c->ck_every = checkpoint_every;
+  c->rec_t0 = t0;
+  c->rec_n = n;
+  return LBM_OK;
+}
+
+lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dgamma, double* drho0) {
+  if (!c || !drho) return c ? fail(c, LBM_ERR_ARG, "drho is NULL") : LBM_ERR_ARG;
+  if (c->rec_t0 < 0 || c->rec_t0 + c->rec_n != c->t)
+    return fail(c, LBM_ERR_ARG, "no recording ends at the current step (call lbm_record)");
+  const lbm::AdjFns* A = lbm::adj_fns(c->Q, c->nc, c->precision);
+  const int64_t N = c->P.N;
+  const int nc = c->nc, Q = c->Q, K = c->ck_every;
+  const size_t sbytes = lbm_state_bytes(c), lbytes = (size_t)nc * Q * N * A->real_bytes;
+  const unsigned nblk = (unsigned)((N + 255) / 256);
+  std::vector<void*> snaps((size_t)K, nullptr);
+  void *la = nullptr, *lb = nullptr, *Fb = nullptr, *jb = nullptr, *rb = nullptr;
+  double *gpart = nullptr, *kpart = nullptr, *dd = nullptr;
+  int* st_s = nullptr;
+  long long* t_s = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** p, size_t b) {
+    if (e == cudaSuccess) e = cudaMalloc(p, b);
+  };
+  for (auto& p : snaps) alloc(&p, sbytes);
+  alloc(&la, lbytes);
+  alloc(&lb, lbytes);
+  alloc(&Fb, (size_t)3 * N * A->real_bytes);
+  alloc(&jb, (size_t)3 * N * A->real_bytes);
+  alloc(&rb, (size_t)nc * N * A->real_bytes);
+  alloc((void**)&gpart, (size_t)nblk * nc * sizeof(double));
+  alloc((void**)&kpart, (size_t)nblk * nc * nc * sizeof(double));
+  alloc((void**)&dd, (size_t)nc * N * sizeof(double));
+  alloc((void**)&st_s, sizeof(int));
+  alloc((void**)&t_s, sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(gpart, 0, (size_t)nblk * nc * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(kpart, 0, (size_t)nblk * nc * nc * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(Fb, 0, (size_t)3 * N * A->real_bytes, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(jb, 0, (size_t)3 * N * A->real_bytes, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st_s, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dd, drho, (size_t)nc * N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) {
+    A->seed(c->P, dd, la, c->stream);
+    e = cudaGetLastError();
+  }
+  const int nseg = (int)c->ckpt.size();
+  for (int k = nseg - 1; k >= 0 && e == cudaSuccess; --k) {
+    const int64_t tk = c->rec_t0 + (int64_t)k * K;
+    const int len = (int)std::min<int64_t>(K, c->rec_t0 + c->rec_n - tk);
+    // recompute the segment's states t_k .. t_k + len - 1 from its checkpoint
+    e = cudaMemcpyAsync(snaps[0], c->ckpt[k], sbytes, cudaMemcpyDeviceToDevice, c->stream);
+    for (int i = 1; i < len && e == cudaSuccess; ++i) {
+      e = cudaMemcpyAsync(snaps[i], snaps[i - 1], sbytes, cudaMemcpyDeviceToDevice, c->stream);
+      const int parity = (int)((tk + i - 1) & 1);
+      c->ops->psi(c->P, snaps[i], c->psi, st_s, parity, c->stream);
+      c->ops->collide(c->P, snaps[i], c->psi, st_s, t_s, parity, c->stream);
+      if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    // reverse steps
+    for (int i = len - 1; i >= 0 && e == cudaSuccess; --i) {
+      const int parity = (int)((tk + i) & 1);
+      c->ops->psi(c->P, snaps[i], c->psi, st_s, parity, c->stream);
+      A->pass_a(c->P, snaps[i], c->psi, la, Fb, jb, rb, parity, gpart, c->stream);
+      A->pass_b(c->P, snaps[i], c->psi, la, Fb, jb, rb, lb, parity, kpart, c->stream);
+      std::swap(la, lb);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess && drho0) {
+    A->init_grad(c->P, la, dd, c->stream);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(drho0, dd, (size_t)nc * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  }
+  std::vector<double> hg((size_t)nblk * nc), hk((size_t)nblk * nc * nc);
+  int hst = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hg.data(), gpart, hg.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hk.data(), kpart, hk.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hst, st_s, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  for (auto& p : snaps) cudaFree(p);
+  cudaFree(la);
+  cudaFree(lb);
+  cudaFree(Fb);
+  cudaFree(jb);
+  cudaFree(rb);
+  cudaFree(gpart);
+  cudaFree(kpart);
+  cudaFree(dd);
+  cudaFree(st_s);
+  cudaFree(t_s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lbm_adjoint");
+  if (hst) return fail(c, LBM_ERR_PSI_DOMAIN, "recomputed forward step left the EOS domain");
+  if (dgamma)
+    for (int i = 0; i < nc; ++i) {
+      double acc = 0;
+      for (unsigned bb = 0; bb < nblk; ++bb) acc += hg[(size_t)bb * nc + i];
+      dgamma[i] = acc;
+    }
+  if (dkij)
+    for (int i = 0; i < nc * nc; ++i) {
+      double acc = 0;
+      for (unsigned bb = 0; bb < nblk; ++bb) acc += hk[(size_t)bb * nc * nc + i];
+      dkij[i] = acc;
+    }
   return LBM_OK;
 }
 

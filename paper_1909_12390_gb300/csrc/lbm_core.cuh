@@ -110,6 +110,7 @@ __host__ __device__ constexpr int mnorm(int k) {
 struct Params {
   int nx, ny, nz;
   int64_t N;  // nx * ny * nz
+  uint32_t N32;
   int nc;
   // collision
   double omega;      // 1 / tau
@@ -179,15 +180,17 @@ struct PC<float> {
 enum : int { ST_PSI_DOMAIN = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4 };
 
 // ---------------------------------------------------------------------------------------
-// Site coordinates and periodic neighbours.
+// Site coordinates and periodic neighbours. Site indices are 32-bit: the host requires
+// Q * N < 2^32 (offsets inside one component's block of Q * N populations).
 struct Site {
+  uint32_t idx;
   int x, y, z;
   int xm, xp, ym, yp, zm, zp;
-  __device__ __forceinline__ void set(const Params& P, int64_t idx) {
-    x = (int)(idx % P.nx);
-    int64_t r = idx / P.nx;
-    y = (int)(r % P.ny);
-    z = (int)(r / P.ny);
+  __device__ __forceinline__ void set_xyz(const Params& P, int x_, int y_, int z_) {
+    x = x_;
+    y = y_;
+    z = z_;
+    idx = ((uint32_t)z * (uint32_t)P.ny + (uint32_t)y) * (uint32_t)P.nx + (uint32_t)x;
     xm = x == 0 ? P.nx - 1 : x - 1;
     xp = x == P.nx - 1 ? 0 : x + 1;
     ym = y == 0 ? P.ny - 1 : y - 1;
@@ -195,12 +198,16 @@ struct Site {
     zm = z == 0 ? P.nz - 1 : z - 1;
     zp = z == P.nz - 1 ? 0 : z + 1;
   }
-  // linear index of x + s * e (s = +1 or -1) for a direction with components (ex, ey, ez)
-  __device__ __forceinline__ int64_t nb(const Params& P, int ex, int ey, int ez) const {
-    int xx = ex == 0 ? x : (ex > 0 ? xp : xm);
-    int yy = ey == 0 ? y : (ey > 0 ? yp : ym);
-    int zz = ez == 0 ? z : (ez > 0 ? zp : zm);
-    return ((int64_t)zz * P.ny + yy) * P.nx + xx;
+  __device__ __forceinline__ void set(const Params& P, uint32_t i) {
+    const uint32_t r = i / (uint32_t)P.nx;
+    set_xyz(P, (int)(i - r * (uint32_t)P.nx), (int)(r % (uint32_t)P.ny), (int)(r / (uint32_t)P.ny));
+  }
+  // linear index of the site x + (ex, ey, ez), each component in {-1, 0, 1}
+  __device__ __forceinline__ uint32_t nb(const Params& P, int ex, int ey, int ez) const {
+    const int xx = ex == 0 ? x : (ex > 0 ? xp : xm);
+    const int yy = ey == 0 ? y : (ey > 0 ? yp : ym);
+    const int zz = ez == 0 ? z : (ez > 0 ? zp : zm);
+    return ((uint32_t)zz * (uint32_t)P.ny + (uint32_t)yy) * (uint32_t)P.nx + (uint32_t)xx;
   }
 };
 
@@ -208,24 +215,29 @@ struct Site {
 // slot (x, opp a) holds f*_a(x) = f_a(x + e_a, t + 1), so at odd t f_a(x) sits in slot
 // (x - e_a, opp a); the odd step writes f*_a(x) to slot (x + e_a, a), which restores the even
 // layout. Each site reads and writes the same slots, so no two threads touch one slot.
+// Offsets are relative to the start of one component's block of Q * N values; PAR is the
+// parity of the step (a template argument, so each kernel is compiled once per parity).
 template <int Q>
 struct AA {
-  template <int A>
-  __device__ __forceinline__ static int64_t read_slot(const Params& P, const Site& s, int64_t idx,
-                                                      int parity, int comp) {
+  template <int A, int PAR>
+  __device__ __forceinline__ static uint32_t rd(const Params& P, const Site& s) {
     constexpr int O = Lat<Q>::opp(A);
-    if (parity == 0) return ((int64_t)comp * Q + A) * P.N + idx;
-    return ((int64_t)comp * Q + O) * P.N +
-           s.nb(P, -Lat<Q>::e(A, 0), -Lat<Q>::e(A, 1), -Lat<Q>::e(A, 2));
+    if constexpr (PAR == 0) return (uint32_t)A * P.N32 + s.idx;
+    return (uint32_t)O * P.N32 + s.nb(P, -Lat<Q>::e(A, 0), -Lat<Q>::e(A, 1), -Lat<Q>::e(A, 2));
   }
-  template <int A>
-  __device__ __forceinline__ static int64_t write_slot(const Params& P, const Site& s, int64_t idx,
-                                                       int parity, int comp) {
+  template <int A, int PAR>
+  __device__ __forceinline__ static uint32_t wr(const Params& P, const Site& s) {
     constexpr int O = Lat<Q>::opp(A);
-    if (parity == 0) return ((int64_t)comp * Q + O) * P.N + idx;
-    return ((int64_t)comp * Q + A) * P.N + s.nb(P, Lat<Q>::e(A, 0), Lat<Q>::e(A, 1), Lat<Q>::e(A, 2));
+    if constexpr (PAR == 0) return (uint32_t)O * P.N32 + s.idx;
+    return (uint32_t)A * P.N32 + s.nb(P, Lat<Q>::e(A, 0), Lat<Q>::e(A, 1), Lat<Q>::e(A, 2));
   }
 };
+
+// Start of component c's block of Q * N populations.
+template <int Q, class T>
+__device__ __forceinline__ T* comp_base(T* f, const Params& P, int c) {
+  return f + (size_t)c * Q * P.N;
+}
 
 // Compile-time loop.
 template <int I, int N>

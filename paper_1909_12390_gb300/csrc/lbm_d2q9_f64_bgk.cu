@@ -1,0 +1,6 @@
+// D2Q9, FP64 storage, BGK collision: step, set-up and read-back kernels for 1..4 components.
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+const Ops* ops_q9_f64_bgk(int nc) { return ops_nc<9, PrecF64, 0>(nc); }
+}  // namespace lbm

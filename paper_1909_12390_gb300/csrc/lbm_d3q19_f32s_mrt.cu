@@ -1,0 +1,6 @@
+// D3Q19, FP32-shifted storage, MRT collision: step, set-up and read-back kernels for 1..4 components.
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+const Ops* ops_q19_f32s_mrt(int nc) { return ops_nc<19, PrecF32S, 1>(nc); }
+}  // namespace lbm

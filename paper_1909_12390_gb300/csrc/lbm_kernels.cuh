@@ -30,17 +30,25 @@ struct PrecF32S {
 
 constexpr int kBlock = 256;
 
+// Population stores are marked evict-first: the written populations are not read again in
+// the step, and keeping them out of the way leaves L2 to the populations still to be read.
+template <class Prec>
+__device__ __forceinline__ void store_pop(typename Prec::S* p, typename Prec::R v) {
+  __stcs(p, (typename Prec::S)v);
+}
+
 // ---------------------------------------------------------------------------------------
 // S1-S3 of one site: cell-volume densities, mixture Peng-Robinson EOS, pseudo-potential.
 // Returns 0 or status bits; psi_out is 0 on error.
-template <int Q, int NC, class Prec>
+template <int Q, int NC, class Prec, int PAR>
 __device__ __forceinline__ int site_psi(const Params& P, const typename Prec::S* __restrict__ f, const Site& s,
-                                        int64_t idx, int parity, typename Prec::PsiT& psi_out) {
+                                        typename Prec::PsiT& psi_out) {
   using R = typename Prec::R;
   R d[NC];
   For<0, NC>::run([&]<int C>() {
+    const typename Prec::S* fc = comp_base<Q>(f, P, C);
     R acc = 0;
-    For<0, Q>::run([&]<int A>() { acc += (R)f[AA<Q>::template read_slot<A>(P, s, idx, parity, C)]; });
+    For<0, Q>::run([&]<int A>() { acc += (R)fc[AA<Q>::template rd<A, PAR>(P, s)]; });
     d[C] = acc;
   });
   R rho_t = 0;
@@ -80,9 +88,9 @@ __device__ __forceinline__ int site_psi(const Params& P, const typename Prec::S*
 
 // S4-S6 of one site given psi at the site (pn[0]) and its Q - 1 neighbours (pn[a] at x + e_a):
 // total force, split, Guo-forced BGK or MRT collision, in-place AA write.
-template <int Q, int NC, class Prec, int MRT>
+template <int Q, int NC, class Prec, int MRT, int PAR>
 __device__ __forceinline__ void site_collide(const Params& P, typename Prec::S* __restrict__ f, const Site& s,
-                                             int64_t idx, int parity, const typename Prec::R (&pn)[Q]) {
+                                             const typename Prec::R (&pn)[Q]) {
   using R = typename Prec::R;
   using L = Lat<Q>;
   constexpr int D = L::D;
@@ -108,9 +116,10 @@ __device__ __forceinline__ void site_collide(const Params& P, typename Prec::S* 
   // and total momentum j. The second pass (per component, below) reloads them from L1.
   R dl[NC], j[3] = {0, 0, 0};
   For<0, NC>::run([&]<int C>() {
+    const typename Prec::S* fc = comp_base<Q>(f, P, C);
     R acc = 0;
     For<0, Q>::run([&]<int A>() {
-      const R v = (R)f[AA<Q>::template read_slot<A>(P, s, idx, parity, C)];
+      const R v = (R)fc[AA<Q>::template rd<A, PAR>(P, s)];
       acc += v;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
@@ -159,9 +168,10 @@ __device__ __forceinline__ void site_collide(const Params& P, typename Prec::S* 
   const R igs = (R)1 / gs;
   For<0, NC>::run([&]<int C>() {
     const R chi = PC<R>::gamma(P, C) * rc[C] * igs;  // S5
+    typename Prec::S* fc = comp_base<Q>(f, P, C);
     R g[Q], out[Q];
     For<0, Q>::run([&]<int A>() {
-      const R v = (R)f[AA<Q>::template read_slot<A>(P, s, idx, parity, C)];
+      const R v = (R)fc[AA<Q>::template rd<A, PAR>(P, s)];
       // non-equilibrium part: f - f_eq in the stored (shifted) variables
       g[A] = v - (R)L::w(A) * (dl[C] + rc[C] * Pa[A]);
       out[A] = v - om * g[A] + gk * chi * Fb[A];
@@ -186,53 +196,69 @@ __device__ __forceinline__ void site_collide(const Params& P, typename Prec::S* 
         }
       }
     }
-    For<0, Q>::run([&]<int A>() {
-      f[AA<Q>::template write_slot<A>(P, s, idx, parity, C)] = (typename Prec::S)out[A];
-    });
+    For<0, Q>::run([&]<int A>() { store_pop<Prec>(fc + AA<Q>::template wr<A, PAR>(P, s), out[A]); });
   });
 }
 
 // ---------------------------------------------------------------------------------------
 // Two-kernel step.
 
-// Pass 1: S1-S3 of every site.
-template <int Q, int NC, class Prec>
-__global__ void __launch_bounds__(kBlock) k_psi(const Params P, const typename Prec::S* __restrict__ f,
-                                                typename Prec::PsiT* __restrict__ psi, int* status,
-                                                int parity) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= P.N) return;
-  if (*(volatile int*)status) return;
+// Pass 1: S1-S3 of every site. Grid (x blocks, y, z), one site per thread.
+template <int Q, int NC, class Prec, int PAR>
+__device__ __forceinline__ void psi_body(const Params& P, const typename Prec::S* __restrict__ f,
+                                         typename Prec::PsiT* __restrict__ psi, int* status, int x) {
   Site s;
-  s.set(P, idx);
+  s.set_xyz(P, x, blockIdx.y, blockIdx.z);
   typename Prec::PsiT v;
-  int e = site_psi<Q, NC, Prec>(P, f, s, idx, parity, v);
+  const int e = site_psi<Q, NC, Prec, PAR>(P, f, s, v);
   if (e) {
     atomicOr(status, e);
     return;
   }
-  psi[idx] = v;
+  psi[s.idx] = v;
+}
+
+template <int Q, int NC, class Prec>
+__global__ void __launch_bounds__(kBlock) k_psi(const Params P, const typename Prec::S* __restrict__ f,
+                                                typename Prec::PsiT* __restrict__ psi, int* status,
+                                                int parity) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= P.nx) return;
+  if (*(volatile int*)status) return;
+  if (parity)
+    psi_body<Q, NC, Prec, 1>(P, f, psi, status, x);
+  else
+    psi_body<Q, NC, Prec, 0>(P, f, psi, status, x);
 }
 
 // Pass 2: S4-S6 of every site; psi of the neighbours from global memory.
-template <int Q, int NC, class Prec, int MRT>
-__global__ void __launch_bounds__(kBlock, 2) k_collide(const Params P, typename Prec::S* __restrict__ f,
-                                                    const typename Prec::PsiT* __restrict__ psi,
-                                                    const int* status, long long* t_dev, int parity) {
+template <int Q, int NC, class Prec, int MRT, int PAR>
+__device__ __forceinline__ void collide_body(const Params& P, typename Prec::S* __restrict__ f,
+                                             const typename Prec::PsiT* __restrict__ psi, int x) {
   using R = typename Prec::R;
   using L = Lat<Q>;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= P.N) return;
-  if (*(volatile const int*)status) return;
-  // the step counter advances only for steps whose pseudo-potential pass succeeded
-  if (idx == 0) *t_dev += 1;
   Site s;
-  s.set(P, idx);
+  s.set_xyz(P, x, blockIdx.y, blockIdx.z);
   R pn[Q];
-  pn[0] = (R)psi[idx];
+  pn[0] = (R)psi[s.idx];
 #pragma unroll
   for (int a = 1; a < Q; ++a) pn[a] = (R)psi[s.nb(P, L::e(a, 0), L::e(a, 1), L::e(a, 2))];
-  site_collide<Q, NC, Prec, MRT>(P, f, s, idx, parity, pn);
+  site_collide<Q, NC, Prec, MRT, PAR>(P, f, s, pn);
+}
+
+template <int Q, int NC, class Prec, int MRT>
+__global__ void __launch_bounds__(kBlock, 2) k_collide(const Params P, typename Prec::S* __restrict__ f,
+                                                       const typename Prec::PsiT* __restrict__ psi,
+                                                       const int* status, long long* t_dev, int parity) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= P.nx) return;
+  if (*(volatile const int*)status) return;
+  // the step counter advances only for steps whose pseudo-potential pass succeeded
+  if (x == 0 && blockIdx.y == 0 && blockIdx.z == 0) *t_dev += 1;
+  if (parity)
+    collide_body<Q, NC, Prec, MRT, 1>(P, f, psi, x);
+  else
+    collide_body<Q, NC, Prec, MRT, 0>(P, f, psi, x);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -280,10 +306,10 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 // wait is bounded anyway). Group j + 1 is read for its psi one iteration before it is
 // collided, so its populations are re-read from L2 (a look-ahead of P planes over the whole
 // grid cross-section: 60 MB for 256^2 sites and 3 FP32 D3Q19 components).
-template <int Q, int NC, class Prec, int MRT>
-__global__ void __launch_bounds__(Fused<Q>::NT, Q == 19 ? 2 : 4)
-    k_fused(const Params P, typename Prec::S* __restrict__ f, typename Prec::PsiT* __restrict__ psi_g, int* status,
-            long long* t_dev, const FusedArgs A) {
+template <int Q, int NC, class Prec, int MRT, int PAR>
+__device__ __forceinline__ void fused_body(const Params& P, typename Prec::S* __restrict__ f,
+                                           typename Prec::PsiT* __restrict__ psi_g, int* status, long long* t_dev,
+                                           const FusedArgs& A, unsigned long long t) {
   using Gm = Fused<Q>;
   using R = typename Prec::R;
   using PsiT = typename Prec::PsiT;
@@ -295,9 +321,6 @@ __global__ void __launch_bounds__(Fused<Q>::NT, Q == 19 ? 2 : 4)
   __shared__ int nbr_need[27];  // 0 = same chunk, 1 = chunk below, 2 = chunk above
   __shared__ int n_nbr;
 
-  if (*(volatile int*)status) return;  // a previous step failed: do nothing
-  const unsigned long long t = (unsigned long long)*(volatile long long*)t_dev;
-  const int parity = (int)(t & 1);
   const int L_ = A.L, G = A.L / NP;
   const unsigned long long base = t * (unsigned long long)G;
   const int b = blockIdx.x;
@@ -326,21 +349,24 @@ __global__ void __launch_bounds__(Fused<Q>::NT, Q == 19 ? 2 : 4)
     n_nbr = n;
   }
 
-  auto site_index = [&](int m) -> int64_t {
-    return D3 ? ((int64_t)m * P.ny + cy) * P.nx + cx : (int64_t)m * P.nx + cx;
+  auto site_at = [&](int m, Site& st) {
+    if constexpr (D3)
+      st.set_xyz(P, cx, cy, m);
+    else
+      st.set_xyz(P, cx, m, 0);
   };
   int err = 0;
   // stage s: psi of the NP planes of group (s == 0 ? G - 1 : s - 1)
   auto stage = [&](int s_) {
     const int g = s_ == 0 ? G - 1 : s_ - 1;
     PsiT v[NP];
-    int64_t ix[NP];
+    uint32_t ix[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-      ix[i] = site_index(p0 + g * NP + i);
       Site st;
-      st.set(P, ix[i]);
-      err |= site_psi<Q, NC, Prec>(P, f, st, ix[i], parity, v[i]);
+      site_at(p0 + g * NP + i, st);
+      ix[i] = st.idx;
+      err |= site_psi<Q, NC, Prec, PAR>(P, f, st, v[i]);
     }
 #pragma unroll
     for (int i = 0; i < NP; ++i) psi_g[ix[i]] = v[i];
@@ -401,9 +427,8 @@ __global__ void __launch_bounds__(Fused<Q>::NT, Q == 19 ? 2 : 4)
 #pragma unroll 1
     for (int i = 0; i < NP; ++i) {
       const int q = j * NP + i;
-      const int64_t idx = site_index(p0 + q);
       Site st;
-      st.set(P, idx);
+      site_at(p0 + q, st);
       R pn[Q];
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
@@ -411,7 +436,7 @@ __global__ void __launch_bounds__(Fused<Q>::NT, Q == 19 ? 2 : 4)
         const int ey = D3 ? L::e(a, 1) : 0;
         pn[a] = (R)win[(q + 1 + em + NS) % NS][D3 ? ly + 1 + ey : 0][lx + 1 + L::e(a, 0)];
       }
-      site_collide<Q, NC, Prec, MRT>(P, f, st, idx, parity, pn);
+      site_collide<Q, NC, Prec, MRT, PAR>(P, f, st, pn);
     }
   }
   if (!ok) err |= ST_TIMEOUT;
@@ -432,6 +457,18 @@ __global__ void __launch_bounds__(Fused<Q>::NT, Q == 19 ? 2 : 4)
       *A.done = 0;
     }
   }
+}
+
+template <int Q, int NC, class Prec, int MRT>
+__global__ void __launch_bounds__(Fused<Q>::NT, Q == 19 ? 2 : 4)
+    k_fused(const Params P, typename Prec::S* __restrict__ f, typename Prec::PsiT* __restrict__ psi_g, int* status,
+            long long* t_dev, const FusedArgs A) {
+  if (*(volatile int*)status) return;  // a previous step failed: do nothing
+  const unsigned long long t = (unsigned long long)*(volatile long long*)t_dev;
+  if (t & 1)
+    fused_body<Q, NC, Prec, MRT, 1>(P, f, psi_g, status, t_dev, A, t);
+  else
+    fused_body<Q, NC, Prec, MRT, 0>(P, f, psi_g, status, t_dev, A, t);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -467,18 +504,27 @@ __global__ void k_init(const Params P, typename Prec::S* f, const double* __rest
 }
 
 // canonical FP64 populations <-> storage
+template <int Q, int NC, class Prec, int PAR>
+__device__ __forceinline__ void get_f_body(const Params& P, const typename Prec::S* __restrict__ f, double* out,
+                                           const Site& s) {
+  For<0, NC>::run([&]<int C>() {
+    const typename Prec::S* fc = comp_base<Q>(f, P, C);
+    For<0, Q>::run([&]<int A>() {
+      out[((int64_t)C * Q + A) * P.N + s.idx] = (double)fc[AA<Q>::template rd<A, PAR>(P, s)] + Lat<Q>::w(A) * P.rho_ref[C];
+    });
+  });
+}
+
 template <int Q, int NC, class Prec>
 __global__ void k_get_f(const Params P, const typename Prec::S* __restrict__ f, double* out, int parity) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= P.N) return;
   Site s;
-  s.set(P, idx);
-  For<0, NC>::run([&]<int C>() {
-    For<0, Q>::run([&]<int A>() {
-      out[((int64_t)C * Q + A) * P.N + idx] =
-          (double)f[AA<Q>::template read_slot<A>(P, s, idx, parity, C)] + Lat<Q>::w(A) * P.rho_ref[C];
-    });
-  });
+  s.set(P, (uint32_t)idx);
+  if (parity)
+    get_f_body<Q, NC, Prec, 1>(P, f, out, s);
+  else
+    get_f_body<Q, NC, Prec, 0>(P, f, out, s);
 }
 
 template <int Q, int NC, class Prec>
@@ -495,20 +541,18 @@ __global__ void k_set_f(const Params P, typename Prec::S* f, const double* __res
 }
 
 // Macroscopic fields of the current state; psi must hold this state's pseudo-potential.
-template <int Q, int NC, class Prec>
-__global__ void k_fields(const Params P, const typename Prec::S* __restrict__ f,
-                         const typename Prec::PsiT* __restrict__ psi, double* rho_out, double* u_out,
-                         double* p_out, double* psi_out, int parity) {
+template <int Q, int NC, class Prec, int PAR>
+__device__ __forceinline__ void fields_body(const Params& P, const typename Prec::S* __restrict__ f,
+                                            const typename Prec::PsiT* __restrict__ psi, double* rho_out,
+                                            double* u_out, double* p_out, double* psi_out, const Site& s) {
   using L = Lat<Q>;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= P.N) return;
-  Site s;
-  s.set(P, idx);
+  const int64_t idx = s.idx;
   double rc[NC], j[3] = {0, 0, 0}, rho = 0;
   For<0, NC>::run([&]<int C>() {
+    const typename Prec::S* fc = comp_base<Q>(f, P, C);
     double acc = 0;
     For<0, Q>::run([&]<int A>() {
-      double v = (double)f[AA<Q>::template read_slot<A>(P, s, idx, parity, C)];
+      double v = (double)fc[AA<Q>::template rd<A, PAR>(P, s)];
       acc += v;
 #pragma unroll
       for (int d = 0; d < L::D; ++d) j[d] += L::e(A, d) * v;
@@ -536,6 +580,20 @@ __global__ void k_fields(const Params P, const typename Prec::S* __restrict__ f,
   }
   if (p_out) p_out[idx] = e.pD / e.Dd;
   if (psi_out) psi_out[idx] = p0;
+}
+
+template <int Q, int NC, class Prec>
+__global__ void k_fields(const Params P, const typename Prec::S* __restrict__ f,
+                         const typename Prec::PsiT* __restrict__ psi, double* rho_out, double* u_out,
+                         double* p_out, double* psi_out, int parity) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P.N) return;
+  Site s;
+  s.set(P, (uint32_t)idx);
+  if (parity)
+    fields_body<Q, NC, Prec, 1>(P, f, psi, rho_out, u_out, p_out, psi_out, s);
+  else
+    fields_body<Q, NC, Prec, 0>(P, f, psi, rho_out, u_out, p_out, psi_out, s);
 }
 
 // Per-component mass: per-block partial sums in FP64, then one block sums the partials,
@@ -572,12 +630,23 @@ struct Launch {
   using S = typename Prec::S;
   using PsiT = typename Prec::PsiT;
   static unsigned blocks(const Params& P) { return (unsigned)((P.N + kBlock - 1) / kBlock); }
+  // site grid of the step passes: x in blocks of up to 256 threads, one block row per (y, z)
+  static void site_grid(const Params& P, dim3& grid, dim3& block) {
+    int tx = 32;
+    while (tx < P.nx && tx < kBlock) tx *= 2;
+    block = dim3(tx);
+    grid = dim3((unsigned)((P.nx + tx - 1) / tx), (unsigned)P.ny, (unsigned)P.nz);
+  }
   static void psi(const Params& P, const void* f, void* ps, int* st, int parity, cudaStream_t s) {
-    k_psi<Q, NC, Prec><<<blocks(P), kBlock, 0, s>>>(P, (const S*)f, (PsiT*)ps, st, parity);
+    dim3 g, b;
+    site_grid(P, g, b);
+    k_psi<Q, NC, Prec><<<g, b, 0, s>>>(P, (const S*)f, (PsiT*)ps, st, parity);
   }
   static void collide(const Params& P, void* f, const void* ps, const int* st, long long* t_dev, int parity,
                       cudaStream_t s) {
-    k_collide<Q, NC, Prec, MRT><<<blocks(P), kBlock, 0, s>>>(P, (S*)f, (const PsiT*)ps, st, t_dev, parity);
+    dim3 g, b;
+    site_grid(P, g, b);
+    k_collide<Q, NC, Prec, MRT><<<g, b, 0, s>>>(P, (S*)f, (const PsiT*)ps, st, t_dev, parity);
   }
   static int fused_max_blocks() {
     int nb = 0, dev = 0, sms = 0;

@@ -29,9 +29,23 @@ struct Ops {
   int fused_group;  // planes per synchronisation round
 };
 
-const Ops* ops_q9_f64(int nc, int collision);
-const Ops* ops_q9_f32s(int nc, int collision);
-const Ops* ops_q19_f64(int nc, int collision);
-const Ops* ops_q19_f32s(int nc, int collision);
+// one translation unit per lattice, storage type and collision
+const Ops* ops_q9_f64_bgk(int nc);
+const Ops* ops_q9_f64_mrt(int nc);
+const Ops* ops_q9_f32s_bgk(int nc);
+const Ops* ops_q9_f32s_mrt(int nc);
+const Ops* ops_q19_f64_bgk(int nc);
+const Ops* ops_q19_f64_mrt(int nc);
+const Ops* ops_q19_f32s_bgk(int nc);
+const Ops* ops_q19_f32s_mrt(int nc);
+
+inline const Ops* ops_get(int Q, int fp32, int mrt, int nc) {
+  if (Q == 9) {
+    if (fp32) return mrt ? ops_q9_f32s_mrt(nc) : ops_q9_f32s_bgk(nc);
+    return mrt ? ops_q9_f64_mrt(nc) : ops_q9_f64_bgk(nc);
+  }
+  if (fp32) return mrt ? ops_q19_f32s_mrt(nc) : ops_q19_f32s_bgk(nc);
+  return mrt ? ops_q19_f64_mrt(nc) : ops_q19_f64_bgk(nc);
+}
 
 }  // namespace lbm

@@ -26,7 +26,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_init", "lbm_step"
            "lbm_step_static", "lbm_step_static_error", "lbm_batch_create", "lbm_batch_destroy",
            "lbm_batch_init", "lbm_batch_step", "lbm_batch_case_status", "lbm_batch_fields",
            "lbm_batch_get_f", "lbm_batch_tune", "lbm_batch_tune_report", "lbm_batch_sites",
-           "lbm_batch_last_error")
+           "lbm_batch_last_error", "lbm_record", "lbm_adjoint")
 STATIC_MAX_SITES = 1048576
 PATH_AUTO, PATH_TWO_KERNEL, PATH_FUSED = 0, 1, 2
 
@@ -109,6 +109,8 @@ def lib() -> ctypes.CDLL:
         L.lbm_batch_sites.restype = ctypes.c_int64
         L.lbm_batch_last_error.argtypes = [vp]
         L.lbm_batch_last_error.restype = ctypes.c_char_p
+        L.lbm_record.argtypes = [vp, ctypes.c_int64, ctypes.c_int]
+        L.lbm_adjoint.argtypes = [vp, _DP, _DP, _DP, _DP]
         L.lbm_last_error.argtypes = [vp]
         L.lbm_last_error.restype = ctypes.c_char_p
         L.lbm_scale_to_lattice.argtypes = [ctypes.c_int, ctypes.POINTER(Component), ctypes.c_double,
@@ -277,6 +279,20 @@ class Lattice:
         n = ctypes.c_int64()
         self._check(lib().lbm_profile_read(self._h, kernel, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+    def record(self, n: int, checkpoint_every: int):
+        """Advance n steps keeping checkpoints for lbm_adjoint."""
+        self._check(lib().lbm_record(self._h, int(n), int(checkpoint_every)))
+
+    def adjoint(self, drho):
+        """Back-propagate dL/drho(final) (array (nc, *grid)) through the recorded steps.
+        Returns (dL/dzeta (nc, nc), dL/dgamma (nc,), dL/drho(start) (nc, *grid))."""
+        d = _f64(drho, self.nc * self.N)
+        dk = np.zeros(self.nc * self.nc)
+        dg = np.zeros(self.nc)
+        d0 = np.empty((self.nc,) + self.grid)
+        self._check(lib().lbm_adjoint(self._h, _dp(d), _dp(dk), _dp(dg), _dp(d0)))
+        return dk.reshape(self.nc, self.nc), dg, d0
 
     def save(self):
         n = int(lib().lbm_state_bytes(self._h))

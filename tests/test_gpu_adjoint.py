@@ -1,0 +1,144 @@
+"""The hand-written adjoint (lbm_record / lbm_adjoint) against the FP64 oracle differentiated
+by forward-mode dual numbers, against central finite differences, and its torch
+autograd.Function."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import lbm_inputs
+import oracle
+from conftest import GOLDEN
+from lbm_cases import comps_of, oracle_case
+
+pytestmark = pytest.mark.gpu
+
+FP64, FP32S = 0, 1
+
+
+@pytest.fixture(scope="module")
+def case5():
+    with open(os.path.join(GOLDEN, "cases.json")) as fh:
+        return json.load(fh)["c5"]
+
+
+def _setup(c, shape, radius):
+    grid = tuple(reversed(shape))
+    rho0 = lbm_inputs.ball_fields(grid, c["rho_l"], c["rho_v"], radius, 4.0,
+                                  center=[g / 2 - 0.35 for g in grid])
+    w = lbm_inputs.uniform01(99, rho0.size).reshape(rho0.shape)
+    return rho0, w
+
+
+def _loss_grad(rho, w):
+    """L = sum w rho^2 / 2 -> dL/drho = w rho."""
+    return 0.5 * float(np.sum(w * rho * rho)), w * rho
+
+
+def _gpu_run(c, shape, rho0, precision, k12, s, steps, K):
+    from paper_1909_12390_gb300 import lbm
+    g = np.array(c["gamma"]) * np.array([s, 1.0])
+    kij = np.array([[0.0, k12], [k12, 0.0]])
+    lat = lbm.Lattice(shape, comps_of(c), T=c["T"], tau=c["tau"], gamma=g, kij=kij, beta=c["beta"],
+                      G=c["G"], precision=precision)
+    lat.init(rho0)
+    lat.record(steps, K)
+    return lat, g
+
+
+def _oracle_grads(c, shape, rho0, w, k12, steps):
+    g = np.array(c["gamma"])
+    oc = oracle_case(dict(c, Q=9), shape, collision=0, kij=[[0.0, k12], [k12, 0.0]], gamma=list(g))
+    f0 = oracle.equilibrium(oc, rho0)
+    df0 = np.zeros((2,) + f0.shape)
+    dk = np.zeros((2, 2, 2))
+    dk[0, 0, 1] = dk[0, 1, 0] = 1.0          # direction 0: d/dk12
+    dg = np.zeros((2, 2))
+    dg[1, 0] = g[0]                           # direction 1: d/ds, gamma_0 = s g_0
+    f, df = oracle.step_dual(oc, f0, df0, dk, dg, steps)
+    rho = f.sum(axis=1)
+    drho = df.sum(axis=2)
+    L, gl = _loss_grad(rho, w)
+    return L, float(np.sum(gl * drho[0])), float(np.sum(gl * drho[1])), rho
+
+
+@pytest.mark.parametrize("K", [7, 1, 60])
+def test_adjoint_fp64_matches_oracle_duals(case5, K):
+    c = case5
+    shape = (32, 24)
+    steps = 60
+    rho0, w = _setup(c, shape, 6.0)
+    k12 = 0.01
+    lat, g = _gpu_run(c, shape, rho0, FP64, k12, 1.0, steps, K)
+    rho = lat.fields(u=False, p=False, psi=False)["rho"]
+    L, gl = _loss_grad(rho, w)
+    dk, dgam, d0 = lat.adjoint(gl)
+    dk12 = dk[0, 1] + dk[1, 0]
+    ds = dgam[0] * g[0]
+    Lo, ok12, os_, rho_o = _oracle_grads(c, shape, rho0, w, k12, steps)
+    assert np.max(np.abs(rho - rho_o) / rho_o) < 1e-11
+    print("K=%d dL/dk12 %.12e (oracle %.12e)  dL/ds %.12e (oracle %.12e)" % (K, dk12, ok12, ds, os_))
+    assert dk12 == pytest.approx(ok12, rel=1e-8)
+    assert ds == pytest.approx(os_, rel=1e-8)
+
+
+def test_adjoint_fp64_matches_central_differences(case5):
+    """Central differences with h = 1e-5 on the FP64 path for zeta_12, s and one initial
+    density direction."""
+    c = case5
+    shape = (32, 24)
+    steps = 40
+    rho0, w = _setup(c, shape, 6.0)
+    k12, s, h = 0.02, 1.0, 1e-5
+
+    def L_of(k, sc, r0):
+        lat, _ = _gpu_run(c, shape, r0, FP64, k, sc, steps, steps)
+        return _loss_grad(lat.fields(u=False, p=False, psi=False)["rho"], w)[0]
+
+    lat, g = _gpu_run(c, shape, rho0, FP64, k12, s, steps, 9)
+    _, gl = _loss_grad(lat.fields(u=False, p=False, psi=False)["rho"], w)
+    dk, dgam, d0 = lat.adjoint(gl)
+    fd_k = (L_of(k12 + h, s, rho0) - L_of(k12 - h, s, rho0)) / (2 * h)
+    fd_s = (L_of(k12, s + h, rho0) - L_of(k12, s - h, rho0)) / (2 * h)
+    v = lbm_inputs.uniform01(7, rho0.size).reshape(rho0.shape) - 0.5
+    fd_r = (L_of(k12, s, rho0 + h * v) - L_of(k12, s, rho0 - h * v)) / (2 * h)
+    assert dk[0, 1] + dk[1, 0] == pytest.approx(fd_k, rel=1e-6)
+    assert dgam[0] * g[0] == pytest.approx(fd_s, rel=1e-6)
+    assert float(np.sum(d0 * v)) == pytest.approx(fd_r, rel=1e-6)
+
+
+def test_adjoint_fp32_matches_fp64_oracle(case5):
+    c = case5
+    shape = (64, 48)
+    steps = 150
+    rho0, w = _setup(c, shape, 12.0)
+    k12 = 0.0
+    lat, g = _gpu_run(c, shape, rho0, FP32S, k12, 1.0, steps, 55)
+    _, gl = _loss_grad(lat.fields(u=False, p=False, psi=False)["rho"], w)
+    dk, dgam, _ = lat.adjoint(gl)
+    Lo, ok12, os_, _ = _oracle_grads(c, shape, rho0, w, k12, steps)
+    print("fp32: dL/dk12 %.6e (oracle %.6e)  dL/ds %.6e (oracle %.6e)" % (dk[0, 1] + dk[1, 0], ok12, dgam[0] * g[0], os_))
+    assert dk[0, 1] + dk[1, 0] == pytest.approx(ok12, rel=2e-3)
+    assert dgam[0] * g[0] == pytest.approx(os_, rel=2e-3)
+
+
+def test_autograd_function_gradients(case5):
+    """torch.autograd.Function wrapper: backward gives the same gradients as the C ABI."""
+    import torch
+    from paper_1909_12390_gb300 import lbm
+    from paper_1909_12390_gb300.autograd import LatticeRun
+    c = case5
+    shape = (32, 24)
+    rho0, w = _setup(c, shape, 6.0)
+    spec = dict(shape=shape, components=comps_of(c), T=c["T"], tau=c["tau"], gamma=c["gamma"],
+                beta=c["beta"], G=c["G"], steps=30, checkpoint_every=8, rho0=rho0, precision=lbm.FP64,
+                pair=(0, 1), least_volatile=1)
+    zeta = torch.tensor(0.01, dtype=torch.float64, requires_grad=True)
+    s = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    rho = LatticeRun.apply(zeta, s, spec)
+    loss = 0.5 * (torch.from_numpy(w) * rho * rho).sum()
+    loss.backward()
+    _, ok12, os_, _ = _oracle_grads(c, shape, rho0, w, 0.01, 30)
+    assert zeta.grad.item() == pytest.approx(ok12, rel=1e-8)
+    assert s.grad.item() == pytest.approx(os_, rel=1e-8)
