@@ -146,8 +146,8 @@ lbm_status lbm_restore(lbm_ctx *ctx, const void *buf, size_t bytes, int64_t t);
  * psi once per site, publishes it plane by plane and collides a plane once its neighbour tiles
  * have published the planes around it (waits are bounded; LBM_ERR_TIMEOUT if one runs out,
  * after which the state is undefined). It needs nx divisible by the tile width (and ny by 8
- * for D3Q19), the marched axis divisible into chunks of at least two groups of 4 planes,
- * and all blocks co-resident. LBM_PATH_TWO_KERNEL runs a pseudo-potential pass and
+ * for D3Q19), the marched axis divisible into chunks of at least two planes, and all blocks
+ * co-resident. LBM_PATH_TWO_KERNEL runs a pseudo-potential pass and
  * a collide-stream pass. LBM_PATH_AUTO (the default at lbm_create) takes the fused path when
  * it fits. Setting LBM_PATH_FUSED on a grid it does not fit returns LBM_ERR_ARG and leaves the
  * two-kernel path. Both paths compute the same arithmetic in the same order per site. */

@@ -52,7 +52,7 @@ __device__ __forceinline__ int batch_step(const Params& P, typename Prec::S* f, 
     pn[0] = (R)psi[idx];
 #pragma unroll
     for (int a = 1; a < Q; ++a) pn[a] = (R)psi[s.nb(P, L::e(a, 0), L::e(a, 1), L::e(a, 2))];
-    site_collide<Q, NC, Prec, MRT, PAR>(P, f, s, pn);
+    site_collide<Q, NC, Prec, MRT, PAR, 0>(P, f, s, pn);  // f may point into shared memory
   }
   __syncthreads();
   return 0;

@@ -30,11 +30,17 @@ struct PrecF32S {
 
 constexpr int kBlock = 256;
 
-// Population stores are marked evict-first: the written populations are not read again in
-// the step, and keeping them out of the way leaves L2 to the populations still to be read.
-template <class Prec>
+// Population stores into global memory are marked evict-first (st.global.cs): the written
+// populations are not read again in the step, and keeping them out of the way leaves L2 to the
+// populations still to be read. GLOBAL = 0 selects a plain (generic) store, required when the
+// populations live in shared memory (the batched kernel): st.global on a shared address is an
+// address-space fault.
+template <class Prec, int GLOBAL>
 __device__ __forceinline__ void store_pop(typename Prec::S* p, typename Prec::R v) {
-  __stcs(p, (typename Prec::S)v);
+  if constexpr (GLOBAL)
+    __stcs(p, (typename Prec::S)v);
+  else
+    *p = (typename Prec::S)v;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -88,7 +94,7 @@ __device__ __forceinline__ int site_psi(const Params& P, const typename Prec::S*
 
 // S4-S6 of one site given psi at the site (pn[0]) and its Q - 1 neighbours (pn[a] at x + e_a):
 // total force, split, Guo-forced BGK or MRT collision, in-place AA write.
-template <int Q, int NC, class Prec, int MRT, int PAR>
+template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1>
 __device__ __forceinline__ void site_collide(const Params& P, typename Prec::S* __restrict__ f, const Site& s,
                                              const typename Prec::R (&pn)[Q]) {
   using R = typename Prec::R;
@@ -196,7 +202,7 @@ __device__ __forceinline__ void site_collide(const Params& P, typename Prec::S* 
         }
       }
     }
-    For<0, Q>::run([&]<int A>() { store_pop<Prec>(fc + AA<Q>::template wr<A, PAR>(P, s), out[A]); });
+    For<0, Q>::run([&]<int A>() { store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<A, PAR>(P, s), out[A]); });
   });
 }
 
@@ -263,15 +269,28 @@ __global__ void __launch_bounds__(kBlock, 2) k_collide(const Params P, typename 
 
 // ---------------------------------------------------------------------------------------
 // Fused step.
+// Compile-time options of the fused step: planes per synchronisation round, the psi stencil
+// from a shared-memory window (1) or straight from L2 (0), and an L2 prefetch of the
+// populations the next round's psi stage reads (1).
+#ifndef LBM_FUSED_P
+#define LBM_FUSED_P 4
+#endif
+#ifndef LBM_FUSED_WINDOW
+#define LBM_FUSED_WINDOW 1
+#endif
+#ifndef LBM_FUSED_PREFETCH
+#define LBM_FUSED_PREFETCH 0
+#endif
+
 template <int Q>
 struct Fused;
 template <>
-struct Fused<19> {  // tile of 32 x 8 sites in (x, y), march along z in groups of 4 planes
-  static constexpr int TX = 32, TY = 8, NT = TX * TY, WY = TY + 2, P = 4;
+struct Fused<19> {  // tile of 32 x 8 sites in (x, y), march along z
+  static constexpr int TX = 32, TY = 8, NT = TX * TY, WY = TY + 2, P = LBM_FUSED_P;
 };
 template <>
-struct Fused<9> {  // tile of 128 sites in x, march along y in groups of 4 rows
-  static constexpr int TX = 128, TY = 1, NT = TX, WY = 1, P = 4;
+struct Fused<9> {  // tile of 128 sites in x, march along y
+  static constexpr int TX = 128, TY = 1, NT = TX, WY = 1, P = LBM_FUSED_P;
 };
 
 struct FusedArgs {
@@ -304,8 +323,10 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 // iteration and every wait refers to stages the neighbours compute before their own wait of
 // the same iteration, so with all blocks co-resident the pipeline cannot deadlock (and every
 // wait is bounded anyway). Group j + 1 is read for its psi one iteration before it is
-// collided, so its populations are re-read from L2 (a look-ahead of P planes over the whole
-// grid cross-section: 60 MB for 256^2 sites and 3 FP32 D3Q19 components).
+// collided, and its populations are meant to be re-read from L2: between the two reads the
+// grid touches about three groups of planes (the collision of group j - 1, reads and writes,
+// and the psi of group j + 1), 45 MB per plane group for 256^2 sites and 3 FP32 D3Q19
+// components, so one plane per group keeps the re-read inside the 129 MB L2.
 template <int Q, int NC, class Prec, int MRT, int PAR>
 __device__ __forceinline__ void fused_body(const Params& P, typename Prec::S* __restrict__ f,
                                            typename Prec::PsiT* __restrict__ psi_g, int* status, long long* t_dev,
@@ -411,7 +432,7 @@ __device__ __forceinline__ void fused_body(const Params& P, typename Prec::S* __
   if (G > 2) stage(2);
   wait(1, 1);  // chunk below: its last group (plane p0 - 1)
   wait(0, 2);  // this chunk's tiles: group 0 (plane p0)
-  if (ok) {
+  if (LBM_FUSED_WINDOW && ok) {
     load_plane(-1);
     load_plane(0);
   }
@@ -422,19 +443,43 @@ __device__ __forceinline__ void fused_body(const Params& P, typename Prec::S* __
     wait(0, j + 3 < G ? j + 3 : G);
     if (j == G - 1) wait(2, 2);
     if (!ok) break;
-    for (int i = 1; i <= NP; ++i) load_plane(j * NP + i);
-    __syncthreads();
+    if constexpr (LBM_FUSED_PREFETCH) {
+      // the populations of group j + 2 (next round's psi stage) into L2
+      if (j + 2 < G) {
+#pragma unroll 1
+        for (int i = 0; i < NP; ++i) {
+          Site st;
+          site_at(p0 + (j + 2) * NP + i, st);
+          For<0, NC>::run([&]<int C>() {
+            const typename Prec::S* fc = comp_base<Q>(f, P, C);
+            For<0, Q>::run([&]<int A>() {
+              asm volatile("prefetch.global.L2 [%0];" ::"l"(fc + AA<Q>::template rd<A, PAR>(P, st)));
+            });
+          });
+        }
+      }
+    }
+    if constexpr (LBM_FUSED_WINDOW) {
+      for (int i = 1; i <= NP; ++i) load_plane(j * NP + i);
+      __syncthreads();
+    }
 #pragma unroll 1
     for (int i = 0; i < NP; ++i) {
       const int q = j * NP + i;
       Site st;
       site_at(p0 + q, st);
       R pn[Q];
+      if constexpr (LBM_FUSED_WINDOW) {
 #pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        const int em = D3 ? L::e(a, 2) : L::e(a, 1);
-        const int ey = D3 ? L::e(a, 1) : 0;
-        pn[a] = (R)win[(q + 1 + em + NS) % NS][D3 ? ly + 1 + ey : 0][lx + 1 + L::e(a, 0)];
+        for (int a = 0; a < Q; ++a) {
+          const int em = D3 ? L::e(a, 2) : L::e(a, 1);
+          const int ey = D3 ? L::e(a, 1) : 0;
+          pn[a] = (R)win[(q + 1 + em + NS) % NS][D3 ? ly + 1 + ey : 0][lx + 1 + L::e(a, 0)];
+        }
+      } else {
+        pn[0] = (R)__ldcg(psi_g + st.idx);
+#pragma unroll
+        for (int a = 1; a < Q; ++a) pn[a] = (R)__ldcg(psi_g + st.nb(P, L::e(a, 0), L::e(a, 1), L::e(a, 2)));
       }
       site_collide<Q, NC, Prec, MRT, PAR>(P, f, st, pn);
     }

@@ -11,7 +11,8 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "liblbm.so")
+# LBM_LIBRARY overrides the library file (e.g. a build with other compile-time tile options)
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(_PKG, "liblbm.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_PSI_DOMAIN, ERR_NONFINITE, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 D2Q9, D3Q19 = 9, 19

@@ -142,3 +142,46 @@ def test_autograd_function_gradients(case5):
     _, ok12, os_, _ = _oracle_grads(c, shape, rho0, w, 0.01, 30)
     assert zeta.grad.item() == pytest.approx(ok12, rel=1e-8)
     assert s.grad.item() == pytest.approx(os_, rel=1e-8)
+
+
+def test_adjoint_full_workload_against_stored_duals(case5):
+    """The adjoint workload at full size: D2Q9 BGK binary droplet 256^2, FP32 forward with the
+    FP64 EOS, 3000 steps, checkpoints every 55 steps; dL/dzeta_12 and dL/ds against the FP64
+    oracle differentiated by dual numbers (tests/golden/make_long_runs.py). Prints the cost of
+    the backward pass relative to the forward run."""
+    import time
+    p = os.path.join(GOLDEN, "long_runs.npz")
+    ref = dict(np.load(p)) if os.path.exists(p) else {}
+    if "adjoint_dk12" not in ref:
+        pytest.skip("long_runs.npz has no adjoint reference")
+    c = case5
+    shape = tuple(c["shape"])
+    grid = tuple(reversed(shape))
+    rho0 = lbm_inputs.ball_fields(grid, c["rho_l"], c["rho_v"], c["init"]["radius"], 4.0)
+    w = lbm_inputs.uniform01(99, rho0.size).reshape(rho0.shape)
+    from paper_1909_12390_gb300 import lbm
+    g = np.array(c["gamma"])
+    lat = lbm.Lattice(shape, comps_of(c), T=c["T"], tau=c["tau"], gamma=g, kij=np.zeros((2, 2)), beta=c["beta"],
+                      G=c["G"], precision=FP32S)
+    lat.init(rho0)
+    lat.step(1)  # warm-up
+    lat.init(rho0)
+    t0 = time.perf_counter()
+    lat.step(int(ref["adjoint_steps"]))
+    t_plain = time.perf_counter() - t0
+    lat.init(rho0)
+    t0 = time.perf_counter()
+    lat.record(int(ref["adjoint_steps"]), c["checkpoint_every"])
+    t_fwd = time.perf_counter() - t0
+    rho = lat.fields(u=False, p=False, psi=False)["rho"]
+    ys, xs = ref["adjoint_sites"]
+    assert float(np.max(np.abs(rho[:, ys, xs] - ref["adjoint_rho"]) / ref["adjoint_rho"].sum(0))) < 2e-4
+    t0 = time.perf_counter()
+    dk, dg, _ = lat.adjoint(w * rho)
+    t_adj = time.perf_counter() - t0
+    dk12, ds = dk[0, 1] + dk[1, 0], dg[0] * g[0]
+    print("adjoint workload: dL/dk12 %.6e (oracle %.6e), dL/ds %.6e (oracle %.6e); forward %.3f s, "
+          "recorded forward %.3f s, backward %.3f s (%.2f x the forward)"
+          % (dk12, ref["adjoint_dk12"], ds, ref["adjoint_ds"], t_plain, t_fwd, t_adj, t_adj / t_plain))
+    assert dk12 == pytest.approx(float(ref["adjoint_dk12"]), rel=5e-3)
+    assert ds == pytest.approx(float(ref["adjoint_ds"]), rel=5e-3)

@@ -269,3 +269,33 @@ def test_full_length_runs_conserve_mass(cases, key):
     assert r[centre] > 0.5 * sum(c["rho_l"])
     assert r[(0,) * r.ndim] < 2.0 * sum(c["rho_v"])
     gpu.close()
+
+
+def _long_runs():
+    p = os.path.join(GOLDEN, "long_runs.npz")
+    return dict(np.load(p)) if os.path.exists(p) else {}
+
+
+def test_droplet_full_length_against_stored_oracle(cases):
+    """The 3-component D2Q9 MRT FP32-shifted droplet for its stated 20000 steps at 512^2 against
+    the FP64 oracle's run of the same case (tests/golden/make_long_runs.py), at 4098 sampled
+    sites, error relative to the local phase density, and the per-component mass."""
+    ref = _long_runs()
+    if "droplet_rho" not in ref:
+        pytest.skip("long_runs.npz has no droplet reference")
+    c = cases["c2"]
+    shape = tuple(c["shape"])
+    gpu = gpu_lattice(c, shape, FP32S)
+    gpu.init(initial_rho(c, shape))
+    gpu.step(int(ref["droplet_steps"]))
+    rg = gpu.fields(u=False, p=False, psi=False)["rho"]
+    ys, xs = ref["droplet_sites"]
+    got = rg[:, ys, xs]
+    want = ref["droplet_rho"]
+    err = float(np.max(np.abs(got - want) / want.sum(0)))
+    err_c = float(np.max(np.abs(got - want) / want))
+    print("droplet 20000 steps: max err %.3e (phase-density relative), %.3e (component relative)" % (err, err_c))
+    assert err < 2e-4
+    m = gpu.mass()
+    assert np.all(np.abs(m / ref["droplet_mass"] - 1) < 1e-4)
+    gpu.close()
