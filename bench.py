@@ -206,6 +206,21 @@ def run_reference(args, rank):
     print(json.dumps(out), flush=True)
 
 
+def max_over_ranks(value, dist, device):
+    """The largest value over all ranks (the job's time is its slowest replica's)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(sites, components, steps, world, ms):
+    """Whole-job component-MLUPS of `world` replicas of `sites` sites each over `ms` ms."""
+    return sites * components * steps * world / (ms / 1e3) / 1e6
+
+
 def batched_variant(stream, steps=1000):
     """The batched flash sweep (512 independent D2Q9 BGK binary slabs of 64-256 x 8 sites,
     FP32-shifted, one block per case in shared memory) timed over `steps` steps after the
@@ -304,13 +319,9 @@ def main():
     fus_ms, fus_n = gpu.profile_read(2)
     gpu.profile(False)
     mass_end = gpu.mass()
-    t_max = ms_total
-    if dist is not None:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(ms_total, dist, "cuda")
     ms_step = t_max / args.steps
-    value = N * nc * args.steps * world / (t_max / 1e3) / 1e6
+    value = job_value(N, nc, args.steps, world, t_max)
 
     # roofline of the dominant kernel: algorithmic bytes are one read and one write of every
     # FP32 population, 2 * 19 * nc * 4 B per site (the fused kernel and the collide pass each
