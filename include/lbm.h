@@ -85,8 +85,11 @@ typedef struct {
                               entries are ignored. NULL with LBM_MRT is an error. */
   int precision;           /* LBM_FP64, or LBM_FP32_SHIFTED: populations stored in FP32 as
                               f_a - w_a rho_ref_s, moments in FP32, every EOS sum in FP64 */
-  const double *rho_ref;   /* nc shift references for LBM_FP32_SHIFTED; NULL means the mean
-                              of each component's density given to lbm_init */
+  const double *rho_ref;   /* nc shift references for LBM_FP32_SHIFTED; NULL means the
+                              minimum of each component's density given to lbm_init (the
+                              vapour value of a two-phase field: vapour populations are then
+                              stored as small deviations, liquid ones at FP32's relative
+                              precision) */
 } lbm_eos;
 
 /* Creates a context for one periodic lattice with nc components (1..4), relaxation time
@@ -104,7 +107,7 @@ lbm_status lbm_set_stream(lbm_ctx *ctx, void *stream);
 
 /* Sets the populations to the equilibrium of Eq. equilibrium(a), f_{s,a} = f_eq(rho_s, u),
  * from host arrays rho[nc][N] and u[3][N] (NULL: u = 0), and the step counter to 0.
- * With LBM_FP32_SHIFTED and rho_ref == NULL the shift references become the component means
+ * With LBM_FP32_SHIFTED and rho_ref == NULL the shift references become the component minima
  * of rho. Densities must be finite and positive. */
 lbm_status lbm_init(lbm_ctx *ctx, const double *rho, const double *u);
 

@@ -385,14 +385,14 @@ lbm_status lbm_batch_init(lbm_batch* b, const double* rho, const double* u) {
     const int64_t N = c.P.N;
     const double* r = rho + (size_t)c.site_off * nc;
     for (int s = 0; s < nc; ++s) {
-      double m = 0;
+      double m = r[s * N];
       for (int64_t k = 0; k < N; ++k) {
         const double v = r[s * N + k];
         if (!(v > 0) || !std::isfinite(v))
           return bfail(b, LBM_ERR_ARG, "case %d: rho must be finite and > 0", i);
-        m += v;
+        m = std::min(m, v);
       }
-      if (b->precision == LBM_FP32_SHIFTED && !b->ref_given[i]) c.P.rho_ref[s] = m / (double)N;
+      if (b->precision == LBM_FP32_SHIFTED && !b->ref_given[i]) c.P.rho_ref[s] = m;
     }
     lbm::finalize_params(c.P);
   }

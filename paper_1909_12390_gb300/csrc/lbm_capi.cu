@@ -494,20 +494,20 @@ lbm_status lbm_init(lbm_ctx* c, const double* rho, const double* u) {
   if (!c) return LBM_ERR_ARG;
   if (!rho) return fail(c, LBM_ERR_ARG, "rho is NULL");
   const int64_t N = c->P.N;
-  double mean[4] = {0, 0, 0, 0};
+  double lo[4] = {0, 0, 0, 0};
   for (int s = 0; s < c->nc; ++s) {
+    lo[s] = rho[s * N];
     for (int64_t i = 0; i < N; ++i) {
       double v = rho[s * N + i];
       if (!(v > 0) || !std::isfinite(v)) return fail(c, LBM_ERR_ARG, "rho[%d][%lld] must be finite and > 0", s, (long long)i);
-      mean[s] += v;
+      lo[s] = std::min(lo[s], v);
     }
-    mean[s] /= (double)N;
   }
   if (u)
     for (int64_t i = 0; i < 3 * N; ++i)
       if (!std::isfinite(u[i])) return fail(c, LBM_ERR_ARG, "u must be finite");
   if (c->precision == LBM_FP32_SHIFTED && !c->ref_given) {
-    for (int s = 0; s < c->nc; ++s) c->P.rho_ref[s] = mean[s];
+    for (int s = 0; s < c->nc; ++s) c->P.rho_ref[s] = lo[s];
     lbm::finalize_params(c->P);
     drop_graph(c);  // the graph holds the parameters by value
   }

@@ -45,6 +45,9 @@ struct Lat<9> {
   // Rows with a free relaxation rate; rho, j and the stress rows relax at 1/tau.
   static constexpr int NK = 4;
   __host__ __device__ static constexpr int krow(int i) { return i == 0 ? 1 : i == 1 ? 2 : i == 2 ? 4 : 6; }
+  // pairs of opposite directions: first member of pair p (the other is opp)
+  static constexpr int NPAIR = 4;
+  __host__ __device__ static constexpr int pfirst(int p) { return p == 0 ? 1 : p == 1 ? 2 : p == 2 ? 5 : 6; }
 };
 
 template <>
@@ -91,6 +94,8 @@ struct Lat<19> {
          : k == 17 ? (e(a, 2) * e(a, 2) - e(a, 0) * e(a, 0)) * e(a, 1)
                    : (e(a, 0) * e(a, 0) - e(a, 1) * e(a, 1)) * e(a, 2);
   }
+  static constexpr int NPAIR = 9;
+  __host__ __device__ static constexpr int pfirst(int p) { return 2 * p + 1; }
   static constexpr int NK = 10;
   __host__ __device__ static constexpr int krow(int i) {
     return i == 0 ? 1 : i == 1 ? 2 : i == 2 ? 4 : i == 3 ? 6 : i == 4 ? 8
@@ -104,6 +109,54 @@ __host__ __device__ constexpr int mnorm(int k) {
   for (int a = 0; a < Q; ++a) s += Lat<Q>::m(k, a) * Lat<Q>::m(k, a);
   return s;
 }
+
+// Pair structure. The Q - 1 moving directions form NPAIR pairs (a, opp(a)), a = pfirst(p).
+// A moment row is even (m(k, opp a) = m(k, a)) or odd (m(k, opp a) = -m(k, a), m(k, 0) = 0):
+// row_parity returns +1, -1, or 0 for neither (no row of either basis).
+template <int Q>
+__host__ __device__ constexpr int row_parity(int k) {
+  bool ev = true, od = Lat<Q>::m(k, 0) == 0;
+  for (int p = 0; p < Lat<Q>::NPAIR; ++p) {
+    const int a = Lat<Q>::pfirst(p), b = Lat<Q>::opp(a);
+    ev = ev && Lat<Q>::m(k, b) == Lat<Q>::m(k, a);
+    od = od && Lat<Q>::m(k, b) == -Lat<Q>::m(k, a);
+  }
+  return ev ? 1 : (od ? -1 : 0);
+}
+// Class of pair p: the axes its directions move along (bit d set when e_d != 0). Entries of the
+// even rows with a free rate (energy, energy square, normal-stress-like rows) depend on e_d^2
+// only, so they take one value per class (the off-diagonal stress rows e_x e_y do not, and
+// relax at 1/tau).
+template <int Q>
+__host__ __device__ constexpr int pclass(int p) {
+  const int a = Lat<Q>::pfirst(p);
+  return (Lat<Q>::e(a, 0) != 0 ? 1 : 0) | (Lat<Q>::e(a, 1) != 0 ? 2 : 0) | (Lat<Q>::e(a, 2) != 0 ? 4 : 0);
+}
+// First pair of class c, or -1.
+template <int Q>
+__host__ __device__ constexpr int crep(int c) {
+  for (int p = 0; p < Lat<Q>::NPAIR; ++p)
+    if (pclass<Q>(p) == c) return p;
+  return -1;
+}
+template <int Q>
+__host__ __device__ constexpr bool pairs_consistent() {
+  int seen = 0;
+  for (int p = 0; p < Lat<Q>::NPAIR; ++p) {
+    const int a = Lat<Q>::pfirst(p), b = Lat<Q>::opp(a);
+    if (a == b || a == 0 || Lat<Q>::opp(b) != a || ((seen >> a) & 1) || ((seen >> b) & 1)) return false;
+    seen |= (1 << a) | (1 << b);
+    for (int i = 0; i < Lat<Q>::NK; ++i) {  // even free rows: one value per class
+      const int k = Lat<Q>::krow(i);
+      if (row_parity<Q>(k) == 1 && Lat<Q>::m(k, a) != Lat<Q>::m(k, Lat<Q>::pfirst(crep<Q>(pclass<Q>(p)))))
+        return false;
+    }
+  }
+  for (int k = 0; k < Q; ++k)
+    if (row_parity<Q>(k) == 0) return false;
+  return seen == (1 << Q) - 2;
+}
+static_assert(pairs_consistent<9>() && pairs_consistent<19>(), "lattice pair tables");
 
 // ---------------------------------------------------------------------------------------
 // Parameters of one lattice, passed by value to every kernel.
@@ -130,7 +183,8 @@ struct Params {
   // constants derived by finalize_params(), in both precisions, so that no kernel converts a
   // parameter per site (an FP64 -> FP32 conversion runs on GB300's 1/72-rate FP64 pipe)
   double gk, c1, c2;  // 1 - omega/2, -beta G, -(1 - beta) G / 2
-  float omega_f, gk_f, c1_f, c2_f, cpsi_f;
+  double k1, k2;      // pair form of the force: -G / 36, -(1 - beta) G / 72 (weights counted in 1/36)
+  float omega_f, gk_f, c1_f, c2_f, cpsi_f, k1_f, k2_f;
   float lam_f[10], rho_ref_f[4], gamma_f[4];
 };
 
@@ -140,6 +194,10 @@ inline void finalize_params(Params& P) {
   P.gk = 1.0 - 0.5 * P.omega;
   P.c1 = -P.beta * P.G;
   P.c2 = -0.5 * (1.0 - P.beta) * P.G;
+  P.k1 = -P.G / 36.0;
+  P.k2 = -0.5 * (1.0 - P.beta) * P.G / 36.0;
+  P.k1_f = (float)P.k1;
+  P.k2_f = (float)P.k2;
   P.omega_f = (float)P.omega;
   P.gk_f = (float)P.gk;
   P.c1_f = (float)P.c1;
@@ -161,6 +219,8 @@ struct PC<double> {
   __device__ __forceinline__ static double gk(const Params& P) { return P.gk; }
   __device__ __forceinline__ static double c1(const Params& P) { return P.c1; }
   __device__ __forceinline__ static double c2(const Params& P) { return P.c2; }
+  __device__ __forceinline__ static double k1(const Params& P) { return P.k1; }
+  __device__ __forceinline__ static double k2(const Params& P) { return P.k2; }
   __device__ __forceinline__ static double lam(const Params& P, int i) { return P.lam[i]; }
   __device__ __forceinline__ static double rho_ref(const Params& P, int i) { return P.rho_ref[i]; }
   __device__ __forceinline__ static double gamma(const Params& P, int i) { return P.gamma[i]; }
@@ -171,6 +231,8 @@ struct PC<float> {
   __device__ __forceinline__ static float gk(const Params& P) { return P.gk_f; }
   __device__ __forceinline__ static float c1(const Params& P) { return P.c1_f; }
   __device__ __forceinline__ static float c2(const Params& P) { return P.c2_f; }
+  __device__ __forceinline__ static float k1(const Params& P) { return P.k1_f; }
+  __device__ __forceinline__ static float k2(const Params& P) { return P.k2_f; }
   __device__ __forceinline__ static float lam(const Params& P, int i) { return P.lam_f[i]; }
   __device__ __forceinline__ static float rho_ref(const Params& P, int i) { return P.rho_ref_f[i]; }
   __device__ __forceinline__ static float gamma(const Params& P, int i) { return P.gamma_f[i]; }

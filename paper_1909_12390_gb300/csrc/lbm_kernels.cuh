@@ -12,6 +12,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "lbm_core.cuh"
 #include "lbm_ops.h"
 
@@ -44,19 +46,12 @@ __device__ __forceinline__ void store_pop(typename Prec::S* p, typename Prec::R 
 }
 
 // ---------------------------------------------------------------------------------------
-// S1-S3 of one site: cell-volume densities, mixture Peng-Robinson EOS, pseudo-potential.
-// Returns 0 or status bits; psi_out is 0 on error.
-template <int Q, int NC, class Prec, int PAR>
-__device__ __forceinline__ int site_psi(const Params& P, const typename Prec::S* __restrict__ f, const Site& s,
-                                        typename Prec::PsiT& psi_out) {
+// S2-S3 of one site from its shifted densities dl_c = rho_c - rho_ref_c: mixture
+// Peng-Robinson EOS and pseudo-potential. Returns 0 or status bits; psi_out is 0 on error.
+template <int NC, class Prec>
+__device__ __forceinline__ int site_psi_dl(const Params& P, const typename Prec::R (&d)[NC],
+                                           typename Prec::PsiT& psi_out) {
   using R = typename Prec::R;
-  R d[NC];
-  For<0, NC>::run([&]<int C>() {
-    const typename Prec::S* fc = comp_base<Q>(f, P, C);
-    R acc = 0;
-    For<0, Q>::run([&]<int A>() { acc += (R)fc[AA<Q>::template rd<A, PAR>(P, s)]; });
-    d[C] = acc;
-  });
   R rho_t = 0;
   double pD, Dd, B;
   if constexpr (sizeof(R) == 8) {
@@ -92,49 +87,114 @@ __device__ __forceinline__ int site_psi(const Params& P, const typename Prec::S*
   return 0;
 }
 
-// S4-S6 of one site given psi at the site (pn[0]) and its Q - 1 neighbours (pn[a] at x + e_a):
-// total force, split, Guo-forced BGK or MRT collision, in-place AA write.
-template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1>
-__device__ __forceinline__ void site_collide(const Params& P, typename Prec::S* __restrict__ f, const Site& s,
-                                             const typename Prec::R (&pn)[Q]) {
+// Shifted densities of one site, summed in the same order as site_moments (rest, then the
+// pairs), so that every path computes bit-identical densities.
+template <int Q, int NC, class Prec, int PAR>
+__device__ __forceinline__ void site_densities(const Params& P, const typename Prec::S* __restrict__ f,
+                                               const Site& s, typename Prec::R (&d)[NC]) {
   using R = typename Prec::R;
   using L = Lat<Q>;
-  constexpr int D = L::D;
-
-  // S4: F = -beta G psi(x) sum_a w_a psi(x+e_a) e_a - (1-beta)/2 G sum_a w_a psi^2(x+e_a) e_a
-  R s1[3] = {0, 0, 0}, s2[3] = {0, 0, 0};
-#pragma unroll
-  for (int a = 1; a < Q; ++a) {
-    R wp = (R)L::w(a) * pn[a];
-    R wq = wp * pn[a];
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      if (L::e(a, d) > 0) { s1[d] += wp; s2[d] += wq; }
-      if (L::e(a, d) < 0) { s1[d] -= wp; s2[d] -= wq; }
-    }
-  }
-  const R c1 = PC<R>::c1(P), c2 = PC<R>::c2(P);
-  R F[3] = {0, 0, 0};
-#pragma unroll
-  for (int d = 0; d < D; ++d) F[d] = c1 * pn[0] * s1[d] + c2 * s2[d];
-
-  // S1 moments, first pass over the populations: shifted densities delta_c = rho_c - rho_ref_c
-  // and total momentum j. The second pass (per component, below) reloads them from L1.
-  R dl[NC], j[3] = {0, 0, 0};
   For<0, NC>::run([&]<int C>() {
     const typename Prec::S* fc = comp_base<Q>(f, P, C);
-    R acc = 0;
-    For<0, Q>::run([&]<int A>() {
-      const R v = (R)fc[AA<Q>::template rd<A, PAR>(P, s)];
-      acc += v;
+    R acc = (R)fc[AA<Q>::template rd<0, PAR>(P, s)];
+    For<0, L::NPAIR>::run([&]<int K>() {
+      constexpr int a = L::pfirst(K), b = L::opp(a);
+      acc += (R)fc[AA<Q>::template rd<a, PAR>(P, s)] + (R)fc[AA<Q>::template rd<b, PAR>(P, s)];
+    });
+    d[C] = acc;
+  });
+}
+
+// S1-S3 of one site: cell-volume densities, mixture Peng-Robinson EOS, pseudo-potential.
+// Returns 0 or status bits; psi_out is 0 on error.
+template <int Q, int NC, class Prec, int PAR>
+__device__ __forceinline__ int site_psi(const Params& P, const typename Prec::S* __restrict__ f, const Site& s,
+                                        typename Prec::PsiT& psi_out) {
+  typename Prec::R d[NC];
+  site_densities<Q, NC, Prec, PAR>(P, f, s, d);
+  return site_psi_dl<NC, Prec>(P, d, psi_out);
+}
+
+// S1 moments of one site: shifted component densities dl_c = sum_a f_ca = rho_c - rho_ref_c
+// and the total momentum j = sum_c sum_a e_a f_ca. The momentum is summed from the differences
+// of opposite populations: near equilibrium the two are close, so in FP32 each difference is
+// exact and j carries no rounding on the scale of the populations.
+template <int Q, int NC, class Prec, int PAR>
+__device__ __forceinline__ void site_moments(const Params& P, const typename Prec::S* __restrict__ f, const Site& s,
+                                             typename Prec::R (&dl)[NC], typename Prec::R (&j)[3]) {
+  using R = typename Prec::R;
+  using L = Lat<Q>;
+  j[0] = j[1] = j[2] = 0;
+  For<0, NC>::run([&]<int C>() {
+    const typename Prec::S* fc = comp_base<Q>(f, P, C);
+    R acc = (R)fc[AA<Q>::template rd<0, PAR>(P, s)];
+    For<0, L::NPAIR>::run([&]<int K>() {
+      constexpr int a = L::pfirst(K), b = L::opp(a);
+      const R va = (R)fc[AA<Q>::template rd<a, PAR>(P, s)];
+      const R vb = (R)fc[AA<Q>::template rd<b, PAR>(P, s)];
+      acc += va + vb;
+      const R d = va - vb;
 #pragma unroll
-      for (int d = 0; d < D; ++d) {
-        if (L::e(A, d) > 0) j[d] += v;
-        if (L::e(A, d) < 0) j[d] -= v;
+      for (int k = 0; k < L::D; ++k) {
+        if (L::e(a, k) > 0) j[k] += d;
+        if (L::e(a, k) < 0) j[k] -= d;
       }
     });
     dl[C] = acc;
   });
+}
+
+// S4-S6 of one site given psi at the site (pn[0]) and its Q - 1 neighbours (pn[a] at x + e_a)
+// and the site's moments: total force, split, Guo-forced BGK or MRT collision, in-place AA
+// write. Everything is arranged over the pairs of opposite directions (a, b = opp(a)):
+//   * the equilibrium is w_a (dl_c + rho_c P_a) with P_a = Pe +- Po (even / odd parts of
+//     3 e.u + 9/2 (e.u)^2 - 3/2 u.u), so its large even part A = w (dl_c + rho_c Pe) is one
+//     value for both members and its rounding cancels in the momentum;
+//   * the Guo term Fb_a = w_a [3 (e_a - u).F + 9 (e_a.u)(e_a.F)] = Fe +- Fo likewise;
+//   * the MRT correction acts on the free rows through pair sums (even rows, one coefficient
+//     per pair class) and pair differences (odd rows);
+//   * the change d_a of each population is formed in full before it is added to the stored
+//     value, so the population is rounded once.
+// In FP32 these keep the rounding of the large quantities out of the momentum balance; a
+// textbook per-direction evaluation lets that rounding drive a random walk of the total
+// momentum, and long runs of a liquid slab then drift measurably.
+template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1>
+__device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S* __restrict__ f, const Site& s,
+                                               const typename Prec::R (&pn)[Q], const typename Prec::R (&dl)[NC],
+                                               const typename Prec::R (&j)[3]) {
+  using R = typename Prec::R;
+  using L = Lat<Q>;
+  constexpr int D = L::D;
+  constexpr int NP = L::NPAIR;
+
+  // S4: F = -beta G psi(x) sum_a w_a psi(x+e_a) e_a - (1-beta)/2 G sum_a w_a psi^2(x+e_a) e_a.
+  // With psi_+ = psi(x + e_p), psi_- = psi(x - e_p) and sum_a w_a e_a = 0 it equals exactly
+  //   F = -G [psi(x) S1 + (1-beta)/2 S2],  S1 = sum_p w_p e_p (psi_+ - psi_-),
+  //                                        S2 = sum_p w_p e_p (psi_+ - psi_-)(psi_+ + psi_- - 2 psi(x)),
+  // whose two terms do not cancel (S2 is a second-difference correction). In FP32 the textbook
+  // form loses several ulps to that cancellation, and the rounding leaves a net force on the
+  // periodic grid (zero in exact arithmetic) that accumulates into a drift of whole interfaces.
+  // Weights are counted in 1/36.
+  R S1[3] = {0, 0, 0}, S2[3] = {0, 0, 0};
+  For<0, NP>::run([&]<int K>() {
+    constexpr int a = L::pfirst(K), b = L::opp(a);
+    constexpr int iw = L::c2(a) == 1 ? (Q == 9 ? 4 : 2) : 1;  // 36 w_a
+    static_assert(iw / 36.0 - L::w(a) < 1e-15 && L::w(a) - iw / 36.0 < 1e-15);
+    const R dp = pn[a] - pn[b];
+    const R dc = dp * ((pn[a] + pn[b]) - (R)2 * pn[0]);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      if (L::e(a, d) != 0) {
+        S1[d] += (R)(iw * L::e(a, d)) * dp;
+        S2[d] += (R)(iw * L::e(a, d)) * dc;
+      }
+    }
+  });
+  const R k1p = PC<R>::k1(P) * pn[0], k2 = PC<R>::k2(P);
+  R F[3] = {0, 0, 0};
+#pragma unroll
+  for (int d = 0; d < D; ++d) F[d] = k1p * S1[d] + k2 * S2[d];
+
   R rc[NC], rho = 0, gs = 0;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
@@ -153,68 +213,137 @@ __device__ __forceinline__ void site_collide(const Params& P, typename Prec::S* 
     uu += u[d] * u[d];
     uF += u[d] * F[d];
   }
-
-  // per-site equilibrium polynomial P_a = 3 e.u + 9/2 (e.u)^2 - 3/2 u.u and the Guo term of the
-  // total force Fb_a = w_a [3 (e_a - u).F + 9 (e_a.u)(e_a.F)]; component s uses chi_s Fb_a.
-  R Pa[Q], Fb[Q];
-#pragma unroll
-  for (int a = 0; a < Q; ++a) {
-    R eu = 0, eF = 0;
+  // Per pair p the even / odd parts of P_a = 3 e.u + 9/2 (e.u)^2 - 3/2 u.u (Pe +- Po) and of
+  // Fb_a = w_a [3 (e_a - u).F + 9 (e_a.u)(e_a.F)] (Fe +- Fo) are formed inside each
+  // component's loop from e_p.u and e_p.F (a few adds; keeping them per site would hold
+  // 2 (Q - 1) more registers through the component loop).
+  auto dot = [&](const R (&v)[3], auto a_) {
+    constexpr int a = decltype(a_)::value;
+    R x = 0;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      if (L::e(a, d) > 0) { eu += u[d]; eF += F[d]; }
-      if (L::e(a, d) < 0) { eu -= u[d]; eF -= F[d]; }
+      if (L::e(a, d) > 0) x += v[d];
+      if (L::e(a, d) < 0) x -= v[d];
     }
-    Pa[a] = eu * ((R)3 + (R)4.5 * eu) - (R)1.5 * uu;
-    Fb[a] = (R)L::w(a) * ((R)3 * (eF - uF) + (R)9 * eu * eF);
-  }
-
+    return x;
+  };
+  const R P0 = -(R)1.5 * uu;
+  const R F0 = -(R)(3.0 * L::w(0)) * uF;
   const R om = PC<R>::omega(P);
   const R gk = PC<R>::gk(P);
   const R igs = (R)1 / gs;
   For<0, NC>::run([&]<int C>() {
+    // Compiler-only barrier: the populations are re-read (from L1) rather than kept in
+    // registers from the moments pass, which would cost Q * NC registers.
+    asm volatile("" ::: "memory");
     const R chi = PC<R>::gamma(P, C) * rc[C] * igs;  // S5
+    const R gkchi = gk * chi;
     typename Prec::S* fc = comp_base<Q>(f, P, C);
-    R g[Q], out[Q];
-    For<0, Q>::run([&]<int A>() {
-      const R v = (R)fc[AA<Q>::template rd<A, PAR>(P, s)];
-      // non-equilibrium part: f - f_eq in the stored (shifted) variables
-      g[A] = v - (R)L::w(A) * (dl[C] + rc[C] * Pa[A]);
-      out[A] = v - om * g[A] + gk * chi * Fb[A];
+    // rest population and the pairs: non-equilibrium part g = f - f_eq (stored variables) and
+    // the BGK + Guo change d = gk chi Fb - omega g. For MRT the free-row moments of
+    // q = g + chi Fb / 2 are accumulated on the way, in pair form (q_a + q_b = gp + chi Fe,
+    // q_a - q_b = gm + chi Fo): even rows through per-class sums, odd rows directly.
+    const R v0 = (R)fc[AA<Q>::template rd<0, PAR>(P, s)];
+    const R g0 = v0 - (R)L::w(0) * (dl[C] + rc[C] * P0);
+    R d0 = gkchi * F0 - om * g0;
+    R da[NP], db[NP];
+    R cs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    R mq[L::NK];
+#pragma unroll
+    for (int i = 0; i < L::NK; ++i) mq[i] = 0;
+    For<0, NP>::run([&]<int K>() {
+      constexpr int a = L::pfirst(K), b = L::opp(a);
+      const R va = (R)fc[AA<Q>::template rd<a, PAR>(P, s)];
+      const R vb = (R)fc[AA<Q>::template rd<b, PAR>(P, s)];
+      const R eu = dot(u, std::integral_constant<int, a>{});
+      const R eF = dot(F, std::integral_constant<int, a>{});
+      const R Pe = (R)4.5 * eu * eu + P0;
+      const R Fe = (R)L::w(a) * ((R)9 * eu * eF - (R)3 * uF);
+      const R Fo = (R)(3.0 * L::w(a)) * eF;
+      const R A = (R)L::w(a) * (dl[C] + rc[C] * Pe);
+      const R B = (R)(3.0 * L::w(a)) * rc[C] * eu;
+      const R ga = (va - A) - B;
+      const R gb = (vb - A) + B;
+      da[K] = gkchi * (Fe + Fo) - om * ga;
+      db[K] = gkchi * (Fe - Fo) - om * gb;
+      if constexpr (MRT) {
+        cs[pclass<Q>(K)] += (ga + gb) + chi * Fe;
+        const R qm = (ga - gb) + chi * Fo;
+        For<0, L::NK>::run([&]<int I>() {
+          constexpr int k = L::krow(I);
+          constexpr int c = L::m(k, a);
+          if constexpr (row_parity<Q>(k) == -1 && c != 0) mq[I] += (R)c * qm;
+        });
+      }
     });
     if constexpr (MRT) {
-      // rows with their own rate: f* -= sum_k M_ka lam_k (M q)_k, q = g + chi Fb / 2
-      R q[Q];
-#pragma unroll
-      for (int a = 0; a < Q; ++a) q[a] = g[a] + (R)0.5 * chi * Fb[a];
-#pragma unroll
-      for (int i = 0; i < L::NK; ++i) {
-        const int k = L::krow(i);
-        R mq = 0;
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-          if (L::m(k, a) != 0) mq += (R)L::m(k, a) * q[a];
+      // d_a -= sum_k M_ka lam_k (M q)_k over the free rows k
+      const R q0 = g0 + (R)0.5 * chi * F0;
+      R lm[L::NK];
+      For<0, L::NK>::run([&]<int I>() {
+        constexpr int k = L::krow(I);
+        R m = mq[I];
+        if constexpr (row_parity<Q>(k) == 1) {
+          if constexpr (L::m(k, 0) != 0) m += (R)L::m(k, 0) * q0;
+          For<1, 8>::run([&]<int CL>() {
+            if constexpr (crep<Q>(CL) >= 0) {
+              constexpr int c = L::m(k, L::pfirst(crep<Q>(CL)));
+              if constexpr (c != 0) m += (R)c * cs[CL];
+            }
+          });
         }
-        mq *= PC<R>::lam(P, i);
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-          if (L::m(k, a) != 0) out[a] -= (R)L::m(k, a) * mq;
-        }
-      }
+        lm[I] = PC<R>::lam(P, I) * m;
+      });
+      // corrections: even part per pair class (and the rest), odd part per pair
+      For<0, L::NK>::run([&]<int I>() {
+        constexpr int k = L::krow(I);
+        if constexpr (row_parity<Q>(k) == 1 && L::m(k, 0) != 0) d0 -= (R)L::m(k, 0) * lm[I];
+      });
+      For<0, NP>::run([&]<int K>() {
+        constexpr int a = L::pfirst(K);
+        R ev = 0, od = 0;
+        For<0, L::NK>::run([&]<int I>() {
+          constexpr int k = L::krow(I);
+          constexpr int c = L::m(k, a);
+          if constexpr (c != 0) {
+            if constexpr (row_parity<Q>(k) == 1)
+              ev += (R)c * lm[I];
+            else
+              od += (R)c * lm[I];
+          }
+        });
+        da[K] -= ev + od;
+        db[K] -= ev - od;
+      });
     }
-    if constexpr (sizeof(R) == 4) {
-      // The weights rounded to FP32 sum to 1 + 7.5e-9 (D2Q9) or 1 + 1.5e-8 (D3Q19), which makes
-      // every step scale the stored deviation rho_c - rho_ref_c by 1 + omega * that excess: a
-      // systematic drift of mass from vapour to liquid. The collision conserves each
-      // component's mass (the mass row is not relaxed and sum_a Fb_a = 0), so the rest
-      // population is set from that invariant instead, leaving only unbiased rounding.
-      R rest = dl[C];
-#pragma unroll
-      for (int a = 1; a < Q; ++a) rest -= out[a];
-      out[0] = rest;
-    }
-    For<0, Q>::run([&]<int A>() { store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<A, PAR>(P, s), out[A]); });
+    // one rounding per stored population (the populations are re-read from L1)
+    asm volatile("" ::: "memory");
+    R rest = dl[C];
+    For<0, NP>::run([&]<int K>() {
+      constexpr int a = L::pfirst(K), b = L::opp(a);
+      const R oa = (R)fc[AA<Q>::template rd<a, PAR>(P, s)] + da[K];
+      const R ob = (R)fc[AA<Q>::template rd<b, PAR>(P, s)] + db[K];
+      if constexpr (sizeof(R) == 4) rest -= oa + ob;
+      store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<a, PAR>(P, s), oa);
+      store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<b, PAR>(P, s), ob);
+    });
+    // The weights rounded to FP32 sum to 1 + 7.5e-9 (D2Q9) or 1 + 1.5e-8 (D3Q19), which makes
+    // every step scale the stored deviation rho_c - rho_ref_c by 1 + omega * that excess: a
+    // systematic drift of mass from vapour to liquid. The collision conserves each component's
+    // mass (the mass row is not relaxed and sum_a Fb_a = 0), so in FP32 the rest population is
+    // set from that invariant instead, leaving only unbiased rounding.
+    const R out0 = sizeof(R) == 4 ? rest : v0 + d0;
+    store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<0, PAR>(P, s), out0);
   });
+}
+
+// S1 and S4-S6 of one site (the moments, then the collision).
+template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1>
+__device__ __forceinline__ void site_collide(const Params& P, typename Prec::S* __restrict__ f, const Site& s,
+                                             const typename Prec::R (&pn)[Q]) {
+  typename Prec::R dl[NC], j[3];
+  site_moments<Q, NC, Prec, PAR>(P, f, s, dl, j);
+  site_collide_m<Q, NC, Prec, MRT, PAR, GLOBAL>(P, f, s, pn, dl, j);
 }
 
 // ---------------------------------------------------------------------------------------
