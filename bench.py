@@ -266,6 +266,8 @@ def main():
                     help="step path of the timed run (default: the library's choice)")
     ap.add_argument("--grid", type=int, default=0,
                     help="cube edge of a smaller case of the same workload (profiling); 0 = 256")
+    ap.add_argument("--nz", type=int, default=0,
+                    help="z extent of a shorter case with the same planes (profiling); 0 = cube")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -291,6 +293,10 @@ def main():
     c = load_case()
     if args.grid:
         c = dict(c, shape=[args.grid] * 3, init=dict(c["init"], radius=48.0 * args.grid / 256))
+    if args.nz:
+        sh = c["shape"]
+        c = dict(c, shape=[sh[0], sh[1], args.nz],
+                 init=dict(c["init"], radius=min(c["init"]["radius"], args.nz / 3.0)))
     nc = len(c["components"])
     N = int(np.prod(c["shape"]))
     rho0 = init_fields(c)
@@ -329,7 +335,9 @@ def main():
     peak, peak_kind = peaks()
     alg_site = 2 * 19 * nc * 4
     if path == lbm.PATH_FUSED:
-        kname, kavg, kinds = "k_fused", fus_ms / max(fus_n, 1), {"k_fused": fus_ms / max(fus_n, 1)}
+        kname = "k_fused3" if gpu.fused_kind == lbm.FUSED_PLANES else "k_fused"
+        kavg = fus_ms / max(fus_n, 1)
+        kinds = {kname: kavg}
     else:
         kname, kavg = "k_collide", col_ms / max(col_n, 1)
         kinds = {"k_psi": psi_ms / max(psi_n, 1), "k_collide": kavg}

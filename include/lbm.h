@@ -144,23 +144,35 @@ size_t lbm_state_bytes(const lbm_ctx *ctx);
 lbm_status lbm_save(lbm_ctx *ctx, void *buf, size_t bytes, int64_t *t);
 lbm_status lbm_restore(lbm_ctx *ctx, const void *buf, size_t bytes, int64_t t);
 
-/* Step path. LBM_PATH_FUSED runs one persistent cooperative kernel per step: each block
- * marches a tile column (32 x 8 sites for D3Q19 along z, 128 sites for D2Q9 along y), computes
- * psi once per site, publishes it plane by plane and collides a plane once its neighbour tiles
- * have published the planes around it (waits are bounded; LBM_ERR_TIMEOUT if one runs out,
- * after which the state is undefined). It needs nx divisible by the tile width (and ny by 8
- * for D3Q19), the marched axis divisible into chunks of at least two planes, and all blocks
- * co-resident. LBM_PATH_TWO_KERNEL runs a pseudo-potential pass and
- * a collide-stream pass. LBM_PATH_AUTO (the default at lbm_create) takes the fused path when
- * it fits. Setting LBM_PATH_FUSED on a grid it does not fit returns LBM_ERR_ARG and leaves the
- * two-kernel path. Both paths compute the same arithmetic in the same order per site. */
+/* Step path. LBM_PATH_FUSED runs one persistent cooperative kernel per step that computes
+ * psi once per site, publishes it plane by plane (release flags) and collides a plane once
+ * the blocks owning its neighbour sites have published the planes around it; waits are
+ * bounded (LBM_ERR_TIMEOUT if one runs out, after which the state is undefined). Two forms:
+ *   LBM_FUSED_PLANES (D3Q19, nz >= 3): two blocks per SM, block b owning a contiguous range
+ *     of every z plane (sites [b nxy / G, (b + 1) nxy / G) of the x-fastest plane index),
+ *     marching z; the populations of a plane are read once from DRAM for psi and the site
+ *     moments, and re-read from L2 for the collision;
+ *   LBM_FUSED_TILES (D2Q9, and D3Q19 grids the first form does not take): each block marches
+ *     a tile column (32 x 8 sites for D3Q19 along z, 128 sites for D2Q9 along y); needs nx
+ *     divisible by the tile width (and ny by 8 for D3Q19) and the marched axis divisible
+ *     into chunks of at least two groups of planes.
+ * Both need all blocks co-resident. LBM_PATH_TWO_KERNEL runs a pseudo-potential pass and a
+ * collide-stream pass. LBM_PATH_AUTO (the default at lbm_create) takes the fused path when it
+ * fits. Setting LBM_PATH_FUSED on a grid it does not fit returns LBM_ERR_ARG and leaves the
+ * two-kernel path. All paths compute the same arithmetic in the same order per site, so their
+ * results are bit-identical. */
 enum { LBM_PATH_AUTO = 0, LBM_PATH_TWO_KERNEL = 1, LBM_PATH_FUSED = 2 };
 lbm_status lbm_set_path(lbm_ctx *ctx, int path);
 /* The path lbm_step takes now (LBM_PATH_TWO_KERNEL or LBM_PATH_FUSED). */
 int lbm_get_path(const lbm_ctx *ctx);
+/* The form of the fused path: LBM_FUSED_TILES or LBM_FUSED_PLANES; 0 on the two-kernel path
+ * or for a NULL ctx. */
+enum { LBM_FUSED_TILES = 1, LBM_FUSED_PLANES = 3 };
+int lbm_get_fused_kind(const lbm_ctx *ctx);
 
 /* Failure-detection test hook, fused path only: from the next step on, fused block `block`
- * (0-based, x-tile fastest, then y-tile, then chunk) computes but never publishes its
+ * (0-based; LBM_FUSED_TILES: x-tile fastest, then y-tile, then chunk; LBM_FUSED_PLANES: the
+ * plane range index) computes but never publishes its
  * progress, so every neighbour's bounded wait runs out and lbm_step returns
  * LBM_ERR_TIMEOUT (within about a second per step, without faulting or hanging the GPU); the
  * populations are then undefined. -1 switches the hook off; lbm_init restores a state. */

@@ -174,7 +174,8 @@ void launch_steps(lbm_ctx* c, int64_t n, int64_t t0) {
         e1 = next_event(c);
       }
       if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], c->stream);
-      cudaError_t e = c->ops->fused(c->P, c->f, c->psi, c->status, c->t_dev, c->fargs, c->stream);
+      cudaError_t e = c->fargs.mode == 3 ? c->ops->fused3(c->P, c->f, c->status, c->t_dev, c->fargs, c->stream)
+                                         : c->ops->fused(c->P, c->f, c->psi, c->status, c->t_dev, c->fargs, c->stream);
       if (e != cudaSuccess && c->launch_err == cudaSuccess) c->launch_err = e;
       if (e1 >= 0) {
         cudaEventRecord(c->ev_pool[e1], c->stream);
@@ -208,8 +209,95 @@ void free_fused(lbm_ctx* c) {
   cudaFree(c->fargs.flags);
   cudaFree(c->fargs.done);
   cudaFree(c->fargs.pending);
+  cudaFree((void*)c->fargs.range);
+  cudaFree((void*)c->fargs.nbr);
+  cudaFree(c->fargs.psi_ring);
   c->fargs = lbm::FusedArgs{};
   c->fused = false;
+}
+
+// Blocks (CTAs) of the active fused kernel.
+int fused_blocks(const lbm_ctx* c) {
+  return c->fargs.mode == 3 ? c->fargs.G : c->fargs.ntx * c->fargs.nty * c->fargs.nchunk;
+}
+
+// The plane-range fused step (k_fused3, D3Q19): G CTAs (two per SM when co-resident), CTA b
+// owning sites [b nxy / G, (b + 1) nxy / G) of every z plane; the neighbour CTAs of each CTA
+// (owners of the 8 in-plane neighbours of its sites) are listed for its waits. Returns false
+// when the grid is too small or a CTA would have more than kF3MaxNbr neighbours.
+bool setup_fused3(lbm_ctx* c) {
+  if (c->Q != 19 || !c->ops->fused3_max_blocks) return false;
+  const int nx = c->P.nx, ny = c->P.ny, nz = c->P.nz;
+  const long long nxy = (long long)nx * ny;
+  if (nz < 3 || nxy < 32) return false;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int G = (int)std::min<long long>(2LL * sms, nxy / 32);
+  int smax = 0;
+  bool fits = false;
+  for (int tries = 0; tries < 4 && G >= 1; ++tries) {
+    smax = (int)((nxy + G - 1) / G);
+    const size_t smem = (size_t)2 * (c->nc + 3) * smax * c->ops->arith_bytes;
+    if (smem > 160 * 1024) return false;
+    const int cap = c->ops->fused3_max_blocks((int)smem);
+    if (cap >= G) {
+      fits = true;
+      break;
+    }
+    if (cap <= 0) return false;
+    G = cap;
+  }
+  if (!fits) return false;
+  std::vector<int> range(G + 1), owner(nxy), nbr((size_t)G * lbm::kF3MaxNbr, -1);
+  for (int b = 0; b <= G; ++b) range[b] = (int)((long long)b * nxy / G);
+  for (int b = 0; b < G; ++b)
+    for (int i = range[b]; i < range[b + 1]; ++i) owner[i] = b;
+  for (int b = 0; b < G; ++b) {
+    int n = 0;
+    for (int i = range[b]; i < range[b + 1]; ++i) {
+      const int x = i % nx, y = i / nx;
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int o = owner[(size_t)((y + dy + ny) % ny) * nx + (x + dx + nx) % nx];
+          if (o == b) continue;
+          bool seen = false;
+          for (int k = 0; k < n; ++k) seen = seen || nbr[(size_t)b * lbm::kF3MaxNbr + k] == o;
+          if (seen) continue;
+          if (n == lbm::kF3MaxNbr) return false;
+          nbr[(size_t)b * lbm::kF3MaxNbr + n++] = o;
+        }
+    }
+  }
+  lbm::FusedArgs a{};
+  a.mode = 3;
+  a.G = G;
+  a.smax = smax;
+  a.silent_block = -1;
+  int* d_range = nullptr;
+  int* d_nbr = nullptr;
+  bool ok = cudaMalloc(&a.flags, (size_t)G * sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMalloc(&a.done, sizeof(unsigned int)) == cudaSuccess && cudaMalloc(&a.pending, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&d_range, (G + 1) * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&d_nbr, nbr.size() * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&a.psi_ring, (size_t)(lbm::kF3Ring + 2) * nxy * c->ops->psi_bytes) == cudaSuccess;
+  a.range = d_range;
+  a.nbr = d_nbr;
+  ok = ok && cudaMemset(a.flags, 0, (size_t)G * sizeof(unsigned long long)) == cudaSuccess &&
+       cudaMemset(a.done, 0, sizeof(unsigned int)) == cudaSuccess && cudaMemset(a.pending, 0, sizeof(int)) == cudaSuccess &&
+       cudaMemcpy(d_range, range.data(), (G + 1) * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+  c->fargs = a;
+  if (!ok) {
+    cudaGetLastError();
+    free_fused(c);
+    return false;
+  }
+  c->fused = true;
+  return true;
 }
 
 // Chooses the fused tiling: tiles of fused_tx x fused_ty sites across the grid, the slowest
@@ -217,6 +305,7 @@ void free_fused(lbm_ctx* c) {
 // whose blocks are still all co-resident. Returns false when the grid does not tile or the blocks would not fit.
 bool setup_fused(lbm_ctx* c) {
   free_fused(c);
+  if (setup_fused3(c)) return true;
   const int TX = c->ops->fused_tx, TY = c->ops->fused_ty;
   const bool d3 = c->Q == 19;
   const int nx = c->P.nx, ny = c->P.ny, nz = c->P.nz;
@@ -254,9 +343,7 @@ bool setup_fused(lbm_ctx* c) {
 // Progress counters must not exceed t * L when the step counter is reset or rewound.
 cudaError_t reset_fused_flags(lbm_ctx* c) {
   if (!c->fused) return cudaSuccess;
-  return cudaMemsetAsync(c->fargs.flags, 0,
-                         (size_t)c->fargs.ntx * c->fargs.nty * c->fargs.nchunk * sizeof(unsigned long long),
-                         c->stream);
+  return cudaMemsetAsync(c->fargs.flags, 0, (size_t)fused_blocks(c) * sizeof(unsigned long long), c->stream);
 }
 
 // Captures kGraphSteps steps starting at an even step; on any capture failure the context
@@ -573,7 +660,7 @@ lbm_status lbm_set_path(lbm_ctx* c, int path) {
 lbm_status lbm_test_silence_block(lbm_ctx* c, int block) {
   if (!c) return LBM_ERR_ARG;
   if (!c->fused) return fail(c, LBM_ERR_ARG, "the fused path is not active");
-  const int nb = c->fargs.ntx * c->fargs.nty * c->fargs.nchunk;
+  const int nb = fused_blocks(c);
   if (block < -1 || block >= nb) return fail(c, LBM_ERR_ARG, "block must be -1 or in [0, %d)", nb);
   CK(c, cudaStreamSynchronize(c->stream));
   drop_graph(c);
@@ -582,6 +669,11 @@ lbm_status lbm_test_silence_block(lbm_ctx* c, int block) {
 }
 
 int lbm_get_path(const lbm_ctx* c) { return c ? (c->fused ? LBM_PATH_FUSED : LBM_PATH_TWO_KERNEL) : -1; }
+
+int lbm_get_fused_kind(const lbm_ctx* c) {
+  if (!c || !c->fused) return 0;
+  return c->fargs.mode == 3 ? LBM_FUSED_PLANES : LBM_FUSED_TILES;
+}
 
 int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
 

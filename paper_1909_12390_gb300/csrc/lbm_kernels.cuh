@@ -439,6 +439,12 @@ struct FusedArgs {
   int* pending;               // status bits raised in the current launch
   int ntx, nty, nchunk, L;    // tiles along x and y (1 in 2-D), chunks and chunk length
   int silent_block;           // test hook: this block publishes no progress (-1: none)
+  // plane-range form (k_fused3, D3Q19)
+  int mode;                   // 1 (or 0): tile columns (k_fused), 3: plane ranges (k_fused3)
+  const int* range;           // G + 1 range starts in the flattened (y, x) index of a plane
+  const int* nbr;             // G x kF3MaxNbr CTAs owning neighbour sites, -1 padded
+  void* psi_ring;             // (kF3Ring + 2) psi planes
+  int G, smax;                // CTAs, largest range
 };
 
 constexpr unsigned kSpinLimit = 1u << 20;  // polls of one flag before giving up (~1 s)
@@ -808,11 +814,18 @@ __global__ void __launch_bounds__(kBlock) k_mass_partial(const Params P, const t
 
 __global__ void k_mass_final(const double* partial, int nblocks, int nc, double* out);
 
+}  // namespace lbm
+
+#include "lbm_fused3.cuh"
+
+namespace lbm {
+
 // ---------------------------------------------------------------------------------------
 // Host launchers and the dispatch table of one (Q, NC, precision, collision).
 template <int Q, int NC, class Prec, int MRT>
 struct Launch {
   using S = typename Prec::S;
+  using R = typename Prec::R;
   using PsiT = typename Prec::PsiT;
   static unsigned blocks(const Params& P) { return (unsigned)((P.N + kBlock - 1) / kBlock); }
   // site grid of the step passes: x in blocks of up to 256 threads, one block row per (y, z)
@@ -853,6 +866,36 @@ struct Launch {
     return cudaLaunchCooperativeKernel((const void*)k_fused<Q, NC, Prec, MRT>, dim3(grid), dim3(Fused<Q>::NT),
                                        args, 0, s);
   }
+  static int fused3_max_blocks(int smem) {
+    if constexpr (Q != 19) {
+      return 0;
+    } else {
+      int nb = 0, dev = 0, sms = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+      if (cudaFuncSetAttribute(k_fused3<NC, Prec, MRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+              cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fused3<NC, Prec, MRT>, kF3Threads, smem) !=
+              cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+      }
+      return nb * sms;
+    }
+  }
+  static cudaError_t fused3(const Params& P, void* f, int* st, long long* t_dev, const FusedArgs& A, cudaStream_t s) {
+    if constexpr (Q != 19) {
+      return cudaErrorNotSupported;
+    } else {
+      S* fp = (S*)f;
+      Params Pc = P;
+      FusedArgs Ac = A;
+      void* args[] = {(void*)&Pc, (void*)&fp, (void*)&st, (void*)&t_dev, (void*)&Ac};
+      const size_t smem = (size_t)2 * (NC + 3) * A.smax * sizeof(R);
+      return cudaLaunchCooperativeKernel((const void*)k_fused3<NC, Prec, MRT>, dim3((unsigned)A.G),
+                                         dim3(kF3Threads), args, smem, s);
+    }
+  }
   static void init(const Params& P, void* f, const double* rho, const double* u, cudaStream_t s) {
     k_init<Q, NC, Prec><<<blocks(P), kBlock, 0, s>>>(P, (S*)f, rho, u);
   }
@@ -873,9 +916,10 @@ struct Launch {
     k_mass_final<<<1, kBlock, 0, s>>>(partial, (int)nb, NC, out);
   }
   static const Ops* table() {
-    static const Ops ops = {psi,           collide,           fused,        fused_max_blocks, init,
-                            get_f,         set_f,             fields,       mass,             (int)sizeof(S),
-                            (int)sizeof(PsiT), Fused<Q>::TX, Fused<Q>::TY, Fused<Q>::P};
+    static const Ops ops = {psi,           collide,           fused,        fused_max_blocks, fused3,
+                            fused3_max_blocks, init,          get_f,        set_f,            fields,
+                            mass,          (int)sizeof(S),    (int)sizeof(PsiT), (int)sizeof(R), Fused<Q>::TX,
+                            Fused<Q>::TY,  Fused<Q>::P};
     return &ops;
   }
 };

@@ -16,6 +16,9 @@ struct Ops {
   cudaError_t (*fused)(const Params&, void* f, void* psi, int* status, long long* t_dev, const FusedArgs&,
                        cudaStream_t);
   int (*fused_max_blocks)();  // co-resident blocks of the fused kernel on this device
+  // plane-range fused step (D3Q19 only; cudaErrorNotSupported / 0 otherwise)
+  cudaError_t (*fused3)(const Params&, void* f, int* status, long long* t_dev, const FusedArgs&, cudaStream_t);
+  int (*fused3_max_blocks)(int smem_bytes);
   void (*init)(const Params&, void* f, const double* rho, const double* u, cudaStream_t);
   void (*get_f)(const Params&, const void* f, double* out, int parity, cudaStream_t);
   void (*set_f)(const Params&, void* f, const double* in, cudaStream_t);
@@ -24,6 +27,7 @@ struct Ops {
   void (*mass)(const Params&, const void* f, double* partial, double* out, cudaStream_t);
   int store_bytes;  // bytes per stored population
   int psi_bytes;    // bytes per stored pseudo-potential value
+  int arith_bytes;  // bytes of the arithmetic type (moments kept by k_fused3)
   int fused_tx;     // fused-kernel tile: sites along x
   int fused_ty;     // and along y (1 for D2Q9)
   int fused_group;  // planes per synchronisation round

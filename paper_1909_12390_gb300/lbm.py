@@ -23,13 +23,14 @@ FP64, FP32_SHIFTED = 0, 1
 EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_init", "lbm_step", "lbm_time",
            "lbm_fields", "lbm_mass", "lbm_get_f", "lbm_set_f", "lbm_state_bytes", "lbm_save",
            "lbm_restore", "lbm_last_error", "lbm_scale_to_lattice", "lbm_profile",
-           "lbm_profile_read", "lbm_set_path", "lbm_get_path", "lbm_test_silence_block",
+           "lbm_profile_read", "lbm_set_path", "lbm_get_path", "lbm_get_fused_kind", "lbm_test_silence_block",
            "lbm_step_static", "lbm_step_static_error", "lbm_batch_create", "lbm_batch_destroy",
            "lbm_batch_init", "lbm_batch_step", "lbm_batch_case_status", "lbm_batch_fields",
            "lbm_batch_get_f", "lbm_batch_tune", "lbm_batch_tune_report", "lbm_batch_sites",
            "lbm_batch_last_error", "lbm_record", "lbm_adjoint")
 STATIC_MAX_SITES = 1048576
 PATH_AUTO, PATH_TWO_KERNEL, PATH_FUSED = 0, 1, 2
+FUSED_TILES, FUSED_PLANES = 1, 3
 
 
 class LBMError(RuntimeError):
@@ -88,6 +89,7 @@ def lib() -> ctypes.CDLL:
         L.lbm_profile_read.argtypes = [vp, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_int64)]
         L.lbm_set_path.argtypes = [vp, ctypes.c_int]
         L.lbm_get_path.argtypes = [vp]
+        L.lbm_get_fused_kind.argtypes = [vp]
         L.lbm_test_silence_block.argtypes = [vp, ctypes.c_int]
         L.lbm_step_static.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.POINTER(Component),
                                       ctypes.POINTER(Eos), ctypes.c_double, vp, ctypes.c_int64, ctypes.c_int64,
@@ -266,6 +268,11 @@ class Lattice:
     @property
     def path(self) -> int:
         return int(lib().lbm_get_path(self._h))
+
+    @property
+    def fused_kind(self) -> int:
+        """FUSED_TILES or FUSED_PLANES on the fused path, else 0."""
+        return int(lib().lbm_get_fused_kind(self._h))
 
     def test_silence_block(self, block: int):
         self._check(lib().lbm_test_silence_block(self._h, int(block)))

@@ -85,13 +85,17 @@ def test_benchmark_grid_takes_the_fused_path(cases):
     c = cases["c3"]
     gpu = gpu_lattice(c, tuple(c["shape"]), FP32S)
     assert gpu.path == lbm.PATH_FUSED
+    assert gpu.fused_kind == lbm.FUSED_PLANES
     gpu.close()
 
 
-def test_fused_rejected_when_the_grid_does_not_tile(cases):
+@pytest.mark.parametrize("shape", [(30, 8, 2), (30, 8)])
+def test_fused_rejected_when_the_grid_does_not_fit(cases, shape):
+    """D3Q19 needs at least 3 planes (the plane-range kernel keeps the first and last plane's
+    psi apart); D2Q9 needs rows that split into 128-site tiles."""
     from paper_1909_12390_gb300 import lbm
-    c = cases["c3"]
-    gpu = gpu_lattice(c, (30, 8, 8), FP32S)
+    c = cases["c3"] if len(shape) == 3 else cases["c2"]
+    gpu = gpu_lattice(c, shape, FP32S)
     assert gpu.path == lbm.PATH_TWO_KERNEL
     with pytest.raises(lbm.LBMError) as ei:
         gpu.set_path(lbm.PATH_FUSED)
