@@ -221,35 +221,36 @@ int fused_blocks(const lbm_ctx* c) {
   return c->fargs.mode == 3 ? c->fargs.G : c->fargs.ntx * c->fargs.nty * c->fargs.nchunk;
 }
 
-// The plane-range fused step (k_fused3, D3Q19): G CTAs (two per SM when co-resident), CTA b
-// owning sites [b nxy / G, (b + 1) nxy / G) of every z plane; the neighbour CTAs of each CTA
-// (owners of the 8 in-plane neighbours of its sites) are listed for its waits. Returns false
-// when the grid is too small or a CTA would have more than kF3MaxNbr neighbours.
+// The plane-range fused step (k_fused3, D3Q19): one CTA per SM of two workers, G workers in
+// all, worker w owning sites [w nxy / G, (w + 1) nxy / G) of every z plane; the neighbour
+// workers of each worker (owners of the 8 in-plane neighbours of its sites) are listed for its
+// waits. Returns false when the grid is too small or a worker would have more than kF3MaxNbr
+// neighbours.
 bool setup_fused3(lbm_ctx* c) {
   if (c->Q != 19 || !c->ops->fused3_max_blocks) return false;
   const int nx = c->P.nx, ny = c->P.ny, nz = c->P.nz;
   const long long nxy = (long long)nx * ny;
-  if (nz < 3 || nxy < 32) return false;
+  if (nz < 3 || nxy < 64) return false;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  int G = (int)std::min<long long>(2LL * sms, nxy / 32);
+  int G = 2 * (int)std::min<long long>(sms, nxy / 64);  // workers, two per CTA
   int smax = 0;
   bool fits = false;
-  for (int tries = 0; tries < 4 && G >= 1; ++tries) {
+  for (int tries = 0; tries < 4 && G >= 2; ++tries) {
     smax = (int)((nxy + G - 1) / G);
-    const size_t smem = (size_t)2 * (c->nc + 3) * smax * c->ops->arith_bytes;
+    const size_t smem = (size_t)2 * (lbm::kF3Lead + 1) * (c->nc + 3) * smax * c->ops->arith_bytes;
     if (smem > 160 * 1024) return false;
-    const int cap = c->ops->fused3_max_blocks((int)smem);
-    if (cap >= G) {
+    const int cap = c->ops->fused3_max_blocks((int)smem);  // co-resident CTAs
+    if (cap >= G / 2) {
       fits = true;
       break;
     }
     if (cap <= 0) return false;
-    G = cap;
+    G = 2 * cap;
   }
   if (!fits) return false;
   std::vector<int> range(G + 1), owner(nxy), nbr((size_t)G * lbm::kF3MaxNbr, -1);

@@ -1,34 +1,71 @@
 // Fused D3Q19 step over plane ranges (k_fused3): one persistent cooperative launch per step.
 //
-// CTA b owns the contiguous range [range[b], range[b+1]) of the flattened (y, x) index of a
-// z plane and marches z = 0 .. nz-1. Iteration k
-//   1. reads the populations of plane k + 1 of its range once from DRAM (the psi stage): the
-//      moments of every site (shifted densities and momentum, kept per thread for the
+// Worker w (two per CTA) owns the contiguous range [range[w], range[w+1]) of the flattened
+// (y, x) index of a z plane and marches z = 0 .. nz-1, with psi computed LEAD planes ahead of the collision
+// (LEAD = LBM_F3_LEAD). Before the march it computes psi of plane nz - 1 and of planes
+// 0 .. LEAD - 1. Iteration k then
+//   1. reads the populations of plane k + LEAD of its range once from DRAM (the psi stage):
+//      the moments of every site (shifted densities and momentum, kept per thread for the
 //      collision) and from them the mixture EOS and psi, written to the psi plane buffer;
-//   2. publishes progress k + 2 (st.release.gpu) and waits (bounded ld.acquire.gpu polls) until
-//      every CTA owning a neighbour site has published it too;
+//   2. publishes its progress (psi done up to plane k + LEAD) with st.release.gpu and waits
+//      (bounded ld.acquire.gpu polls) until every worker owning a neighbour site has psi of
+//      plane k + 1; with LEAD = 2 the neighbours published that an iteration earlier, so they
+//      may lag by one iteration without stalling this worker;
 //   3. collides and streams plane k in place: psi of the 18 neighbours from the plane buffers
-//      (through L2), the populations re-read from L2 (read one iteration before; one plane of
-//      the whole grid is ~45 MB of traffic between the two reads).
+//      (through L2), the populations re-read from L2 (LEAD iterations after the psi stage
+//      read them; one iteration of the whole grid reads ~15 MB at 256^2 sites per plane).
 // psi planes 1 .. nz-2 live in a ring of kF3Ring planes; plane 0 and plane nz-1 have their own
 // buffers because plane nz-1's collision needs plane 0's psi from before the step and plane 0's
 // collision needs plane nz-1's. A site's psi depends only on the populations it reads, and in
 // the AA pattern every site reads and writes its own set of slots, so psi of any site may be
 // computed at any time before that site's collision.
 //
-// Safety of the ring: a CTA writing plane k + 1 in iteration k has seen progress k + 1 from
-// every neighbour, so each neighbour has finished the psi stage of iteration k - 1 and is at
-// least colliding plane k - 1, which reads planes k - 2 .. k: with kF3Ring >= 4 the slot of
-// plane k + 1 is none of them. Deadlock freedom: every CTA publishes stage s before it waits
-// for stage s, and the cooperative launch makes all CTAs co-resident; every wait is bounded
-// anyway (kSpinLimit polls), after which the step reports a timeout.
+// Safety of the ring: a worker writing plane k + LEAD in iteration k has seen (its wait of
+// iteration k - 1) every neighbour's psi of plane k, so each neighbour has passed the psi stage
+// of iteration k - LEAD and collides plane k - LEAD or later, reading planes k - LEAD - 1 and
+// up; with kF3Ring >= 2 LEAD + 2 the slot of plane k + LEAD is none of the planes
+// k - LEAD - 1 .. k + LEAD - 1. Deadlock freedom: every wait targets progress that each
+// neighbour publishes before its own wait of the same or an earlier iteration, and the
+// cooperative launch makes all workers co-resident; every wait is bounded anyway (kSpinLimit
+// polls), after which the step reports a timeout.
 #pragma once
 
 namespace lbm {
 
-constexpr int kF3Threads = 224;  // 7 warps; two CTAs per SM at 144 registers
-constexpr int kF3Ring = 8;       // psi planes in the ring
-constexpr int kF3MaxNbr = 16;    // neighbour CTAs of one CTA
+#ifndef LBM_F3_LEAD
+#define LBM_F3_LEAD 1
+#endif
+// One CTA per SM of two workers, each of 7 warps (kF3Worker threads) with its own plane range,
+// named barriers and progress flag. Worker 1 starts after worker 0's first psi stage, so that
+// in steady state one worker's psi stage (DRAM reads and the FP64 EOS) overlaps the other's
+// collision (FP32 arithmetic and L2 traffic). An SM sub-partition's 16 K registers hold four
+// warps of 128 registers or three of 168: workers of 224 threads (LBM_F3_WORKER) run at 128
+// registers, workers of 192 at 168.
+#ifndef LBM_F3_WORKER
+#define LBM_F3_WORKER 224
+#endif
+constexpr int kF3Worker = LBM_F3_WORKER;
+constexpr int kF3Threads = 2 * kF3Worker;
+constexpr int kF3Bound = kF3Threads <= 384 ? 384 : 512;  // launch bound: 168 or 128 registers
+static_assert(kF3Worker % 32 == 0 && kF3Threads <= 512, "worker size");
+constexpr int kF3Lead = LBM_F3_LEAD;  // planes between the psi stage and the collision
+constexpr int kF3Ring = 8;            // psi planes in the ring
+constexpr int kF3MaxNbr = 16;         // neighbour workers of one worker
+static_assert(kF3Lead >= 1 && kF3Ring >= 2 * kF3Lead + 2, "psi ring too short for the look-ahead");
+
+// Named barrier of one worker (ids 1 and 2; 0 is __syncthreads) and its AND-reduction form.
+__device__ __forceinline__ void f3_bar(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kF3Worker) : "memory");
+}
+__device__ __forceinline__ bool f3_bar_and(int id, bool v) {
+  unsigned r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred p, %2, %3, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"((unsigned)v), "r"(id), "r"(kF3Worker)
+      : "memory");
+  return r != 0;
+}
 
 template <int NC, class Prec, int MRT, int PAR>
 __device__ __forceinline__ void fused3_body(const Params& P, typename Prec::S* __restrict__ f, int* status,
@@ -38,14 +75,20 @@ __device__ __forceinline__ void fused3_body(const Params& P, typename Prec::S* _
   using PsiT = typename Prec::PsiT;
   using L = Lat<Q>;
   extern __shared__ __align__(16) unsigned char f3_smem[];
-  R* mom = reinterpret_cast<R*>(f3_smem);  // [2][NC + 3][smax]: moments of the next two planes
-  __shared__ int nbr[kF3MaxNbr];
-  __shared__ int n_nbr;
+  __shared__ int nbr_s[2][kF3MaxNbr];
+  __shared__ int n_nbr_s[2];
 
-  const int b = blockIdx.x;
-  const int r0 = A.range[b], S = A.range[b + 1] - r0, SM = A.smax;
+  const int half = threadIdx.x >= kF3Worker ? 1 : 0;
+  const int tid = threadIdx.x - half * kF3Worker;
+  const int w = 2 * blockIdx.x + half;  // worker
+  const int bar = 1 + half;
+  const int r0 = A.range[w], S = A.range[w + 1] - r0, SM = A.smax;
+  // [worker][LEAD + 1][NC + 3][smax]: moments of planes k .. k + LEAD
+  R* mom = reinterpret_cast<R*>(f3_smem) + (size_t)half * (kF3Lead + 1) * (NC + 3) * SM;
+  int* nbr = nbr_s[half];
   const int nx = P.nx, nz = P.nz, nxy = P.nx * P.ny;
-  const unsigned long long base = t * (unsigned long long)(nz + 1);
+  // progress value: last plane with psi published + 2, at most nz + LEAD + 1 in a launch
+  const unsigned long long base = t * (unsigned long long)(nz + kF3Lead + 2);
   PsiT* ring = (PsiT*)A.psi_ring;
   auto plane = [&](int z) -> PsiT* {
     z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
@@ -53,12 +96,12 @@ __device__ __forceinline__ void fused3_body(const Params& P, typename Prec::S* _
     if (z == nz - 1) return ring + (size_t)(kF3Ring + 1) * nxy;
     return ring + (size_t)(z % kF3Ring) * nxy;
   };
-  if (threadIdx.x < kF3MaxNbr) nbr[threadIdx.x] = A.nbr[b * kF3MaxNbr + threadIdx.x];
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid < kF3MaxNbr) nbr[tid] = A.nbr[w * kF3MaxNbr + tid];
+  f3_bar(bar);
+  if (tid == 0) {
     int n = 0;
     while (n < kF3MaxNbr && nbr[n] >= 0) ++n;
-    n_nbr = n;
+    n_nbr_s[half] = n;
   }
 
   int err = 0;
@@ -67,7 +110,7 @@ __device__ __forceinline__ void fused3_body(const Params& P, typename Prec::S* _
   auto stage = [&](int z, int buf, bool put, bool keep) {
     PsiT* dst = plane(z);
     R* m = mom + (size_t)buf * (NC + 3) * SM;
-    for (int i = threadIdx.x; i < S; i += kF3Threads) {
+    for (int i = tid; i < S; i += kF3Worker) {
       const int xy = r0 + i;
       Site st;
       st.set_xyz(P, xy % nx, xy / nx, z);
@@ -87,14 +130,14 @@ __device__ __forceinline__ void fused3_body(const Params& P, typename Prec::S* _
     }
   };
   auto publish = [&](int s_) {
-    __syncthreads();
-    if (threadIdx.x == 0 && b != A.silent_block) st_release_u64(&A.flags[b], base + (unsigned long long)s_);
+    f3_bar(bar);
+    if (tid == 0 && w != A.silent_block) st_release_u64(&A.flags[w], base + (unsigned long long)s_);
   };
   auto wait = [&](int s_) {
     bool mine = true;
-    if (ok && threadIdx.x < n_nbr) {
+    if (ok && tid < n_nbr_s[half]) {
       const unsigned long long target = base + (unsigned long long)s_;
-      const unsigned long long* fl = &A.flags[nbr[threadIdx.x]];
+      const unsigned long long* fl = &A.flags[nbr[tid]];
       unsigned it = 0;
       while (ld_acquire_u64(fl) < target) {
         if (++it > kSpinLimit) {
@@ -104,13 +147,13 @@ __device__ __forceinline__ void fused3_body(const Params& P, typename Prec::S* _
         __nanosleep(64);
       }
     }
-    ok = __syncthreads_and(mine && ok) != 0;
+    ok = f3_bar_and(bar, mine && ok);
   };
   auto collide = [&](int z, int buf) {
     const PsiT* pl[3] = {plane(z - 1), plane(z), plane(z + 1)};
     const R* m = mom + (size_t)buf * (NC + 3) * SM;
 #pragma unroll 1
-    for (int i = threadIdx.x; i < S; i += kF3Threads) {
+    for (int i = tid; i < S; i += kF3Worker) {
       const int xy = r0 + i;
       const int x = xy % nx, y = xy / nx;
       Site st;
@@ -133,16 +176,19 @@ __device__ __forceinline__ void fused3_body(const Params& P, typename Prec::S* _
     }
   };
 
-  // stage 1: psi of the last plane (plane 0's collision needs it) and of the first plane
-  if (nz > 1) stage(nz - 1, 0, true, false);
-  stage(0, 0, true, true);
-  publish(1);
+  // worker 1 starts once worker 0 has done its first psi stage (barrier 3 spans the CTA)
+  if (half == 1) asm volatile("bar.sync 3, %0;" ::"r"(kF3Threads) : "memory");
+  stage(nz - 1, 0, true, false);
+  if (half == 0) asm volatile("bar.arrive 3, %0;" ::"r"(kF3Threads) : "memory");
+  for (int p = 0; p < kF3Lead && p < nz; ++p) stage(p, p, p < nz - 1, true);
+  publish(kF3Lead + 1);
   for (int k = 0; k < nz; ++k) {
-    if (k + 1 < nz) stage(k + 1, (k + 1) & 1, k + 1 < nz - 1, true);
-    publish(k + 2);
-    wait(k + 2);
+    const int q = k + kF3Lead;
+    if (q < nz) stage(q, q % (kF3Lead + 1), q < nz - 1, true);
+    publish(q + 2);
+    wait(k + 3);
     if (!ok) break;
-    collide(k, k & 1);
+    collide(k, k % (kF3Lead + 1));
   }
   if (!ok) err |= ST_TIMEOUT;
   // finish: the last CTA of the launch folds the pending status and advances the step
@@ -164,9 +210,9 @@ __device__ __forceinline__ void fused3_body(const Params& P, typename Prec::S* _
   }
 }
 
-// 144 registers: two CTAs of kF3Threads per SM (2 x 224 x 144 <= 65536)
+// One CTA per SM; the launch bound sets the register budget (see kF3Bound).
 template <int NC, class Prec, int MRT>
-__global__ void __maxnreg__(144)
+__global__ void __launch_bounds__(kF3Bound, 1)
     k_fused3(const Params P, typename Prec::S* __restrict__ f, int* status, long long* t_dev, const FusedArgs A) {
   if (*(volatile int*)status) return;  // a previous step failed: do nothing
   const unsigned long long t = (unsigned long long)*(volatile long long*)t_dev;

@@ -115,6 +115,30 @@ __device__ __forceinline__ int site_psi(const Params& P, const typename Prec::S*
   return site_psi_dl<NC, Prec>(P, d, psi_out);
 }
 
+// Hides a value from the optimiser (no instruction): what is computed from it afterwards is
+// not merged with what was computed from it before.
+__device__ __forceinline__ void opaque(float& x) { asm volatile("" : "+f"(x)); }
+__device__ __forceinline__ void opaque(double& x) { asm volatile("" : "+d"(x)); }
+__device__ __forceinline__ void opaque(Site& t) {
+  asm volatile("" : "+r"(t.idx), "+r"(t.x), "+r"(t.y), "+r"(t.z));
+  asm volatile("" : "+r"(t.xm), "+r"(t.xp), "+r"(t.ym), "+r"(t.yp), "+r"(t.zm), "+r"(t.zp));
+}
+
+// Population load that the optimiser keeps where it is written: a plain load of the same
+// address (the moments pass read every population already) would be merged with the earlier
+// one and keep Q * NC values in registers through the collision. Generic addressing, so the
+// same code serves populations in global and in shared memory.
+__device__ __forceinline__ float ld_pop(const float* p) {
+  float v;
+  asm volatile("ld.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_pop(const double* p) {
+  double v;
+  asm volatile("ld.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+
 // S1 moments of one site: shifted component densities dl_c = sum_a f_ca = rho_c - rho_ref_c
 // and the total momentum j = sum_c sum_a e_a f_ca. The momentum is summed from the differences
 // of opposite populations: near equilibrium the two are close, so in FP32 each difference is
@@ -239,34 +263,61 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
     const R chi = PC<R>::gamma(P, C) * rc[C] * igs;  // S5
     const R gkchi = gk * chi;
     typename Prec::S* fc = comp_base<Q>(f, P, C);
-    // rest population and the pairs: non-equilibrium part g = f - f_eq (stored variables) and
-    // the BGK + Guo change d = gk chi Fb - omega g. For MRT the free-row moments of
-    // q = g + chi Fb / 2 are accumulated on the way, in pair form (q_a + q_b = gp + chi Fe,
-    // q_a - q_b = gm + chi Fo): even rows through per-class sums, odd rows directly.
-    const R v0 = (R)fc[AA<Q>::template rd<0, PAR>(P, s)];
-    const R g0 = v0 - (R)L::w(0) * (dl[C] + rc[C] * P0);
-    R d0 = gkchi * F0 - om * g0;
-    R da[NP], db[NP];
-    R cs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    R mq[L::NK];
+    // Non-equilibrium part g = f - f_eq (stored variables) per pair: A is the even part of the
+    // equilibrium (one value for both members), B the odd part; the BGK + Guo change is
+    // d = gk chi Fb - omega g. For MRT a first pass accumulates the free-row moments of
+    // q = g + chi Fb / 2 in pair form (q_a + q_b = g_a + g_b + chi Fe, q_a - q_b =
+    // g_a - g_b + chi Fo; even rows through per-class sums, odd rows directly); the second
+    // pass re-reads the populations (L1), forms d and the MRT correction and stores. Keeping
+    // nothing per pair between the passes holds the register count without spills.
+    // Per-pair values are the same for every component and both passes; the compiler would
+    // compute them once and hold 2 (Q - 1) or more registers through the whole loop. Passing
+    // u, F and u.F through an empty asm makes them opaque per pass, so they are recomputed
+    // (a few FMAs per pair) instead.
+    R uo[3], Fo_[3], uFo = uF, P0o = P0;
+    Site so = s;  // the site's addresses, likewise recomputed per pass
+    auto refresh = [&]() {
+      so = s;
+      opaque(so);
 #pragma unroll
-    for (int i = 0; i < L::NK; ++i) mq[i] = 0;
-    For<0, NP>::run([&]<int K>() {
-      constexpr int a = L::pfirst(K), b = L::opp(a);
-      const R va = (R)fc[AA<Q>::template rd<a, PAR>(P, s)];
-      const R vb = (R)fc[AA<Q>::template rd<b, PAR>(P, s)];
-      const R eu = dot(u, std::integral_constant<int, a>{});
-      const R eF = dot(F, std::integral_constant<int, a>{});
-      const R Pe = (R)4.5 * eu * eu + P0;
-      const R Fe = (R)L::w(a) * ((R)9 * eu * eF - (R)3 * uF);
-      const R Fo = (R)(3.0 * L::w(a)) * eF;
+      for (int d = 0; d < 3; ++d) {
+        uo[d] = u[d];
+        Fo_[d] = F[d];
+        opaque(uo[d]);
+        opaque(Fo_[d]);
+      }
+      uFo = uF;
+      P0o = P0;
+      opaque(uFo);
+      opaque(P0o);
+    };
+    auto pair_g = [&](auto k_, R va, R vb, R& ga, R& gb, R& Fe, R& Fo) {
+      constexpr int a = L::pfirst(decltype(k_)::value);
+      const R eu = dot(uo, std::integral_constant<int, a>{});
+      const R eF = dot(Fo_, std::integral_constant<int, a>{});
+      const R Pe = (R)4.5 * eu * eu + P0o;
+      Fe = (R)L::w(a) * ((R)9 * eu * eF - (R)3 * uFo);
+      Fo = (R)(3.0 * L::w(a)) * eF;
       const R A = (R)L::w(a) * (dl[C] + rc[C] * Pe);
       const R B = (R)(3.0 * L::w(a)) * rc[C] * eu;
-      const R ga = (va - A) - B;
-      const R gb = (vb - A) + B;
-      da[K] = gkchi * (Fe + Fo) - om * ga;
-      db[K] = gkchi * (Fe - Fo) - om * gb;
-      if constexpr (MRT) {
+      ga = (va - A) - B;
+      gb = (vb - A) + B;
+    };
+    const R v0 = (R)ld_pop(fc + AA<Q>::template rd<0, PAR>(P, s));
+    const R g0 = v0 - (R)L::w(0) * (dl[C] + rc[C] * P0);
+    R d0 = gkchi * F0 - om * g0;
+    R lm[L::NK];
+    if constexpr (MRT) {
+      refresh();
+      R cs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      R mq[L::NK];
+#pragma unroll
+      for (int i = 0; i < L::NK; ++i) mq[i] = 0;
+      For<0, NP>::run([&]<int K>() {
+        constexpr int a = L::pfirst(K), b = L::opp(a);
+        R ga, gb, Fe, Fo;
+        pair_g(std::integral_constant<int, K>{}, (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, so)),
+               (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, so)), ga, gb, Fe, Fo);
         cs[pclass<Q>(K)] += (ga + gb) + chi * Fe;
         const R qm = (ga - gb) + chi * Fo;
         For<0, L::NK>::run([&]<int I>() {
@@ -274,12 +325,9 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
           constexpr int c = L::m(k, a);
           if constexpr (row_parity<Q>(k) == -1 && c != 0) mq[I] += (R)c * qm;
         });
-      }
-    });
-    if constexpr (MRT) {
-      // d_a -= sum_k M_ka lam_k (M q)_k over the free rows k
+      });
+      // lam_k (M q)_k over the free rows k
       const R q0 = g0 + (R)0.5 * chi * F0;
-      R lm[L::NK];
       For<0, L::NK>::run([&]<int I>() {
         constexpr int k = L::krow(I);
         R m = mq[I];
@@ -294,13 +342,25 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
         }
         lm[I] = PC<R>::lam(P, I) * m;
       });
-      // corrections: even part per pair class (and the rest), odd part per pair
       For<0, L::NK>::run([&]<int I>() {
         constexpr int k = L::krow(I);
         if constexpr (row_parity<Q>(k) == 1 && L::m(k, 0) != 0) d0 -= (R)L::m(k, 0) * lm[I];
       });
-      For<0, NP>::run([&]<int K>() {
-        constexpr int a = L::pfirst(K);
+      asm volatile("" ::: "memory");  // re-read the populations rather than keep them
+    }
+    // BGK + Guo (+ the MRT correction d_a -= sum_k M_ka lam_k (M q)_k: even part per pair
+    // class, odd part per pair), one rounding per stored population
+    R rest = dl[C];
+    refresh();
+    For<0, NP>::run([&]<int K>() {
+      constexpr int a = L::pfirst(K), b = L::opp(a);
+      const R va = (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, so));
+      const R vb = (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, so));
+      R ga, gb, Fe, Fo;
+      pair_g(std::integral_constant<int, K>{}, va, vb, ga, gb, Fe, Fo);
+      R da = gkchi * (Fe + Fo) - om * ga;
+      R db = gkchi * (Fe - Fo) - om * gb;
+      if constexpr (MRT) {
         R ev = 0, od = 0;
         For<0, L::NK>::run([&]<int I>() {
           constexpr int k = L::krow(I);
@@ -312,20 +372,14 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
               od += (R)c * lm[I];
           }
         });
-        da[K] -= ev + od;
-        db[K] -= ev - od;
-      });
-    }
-    // one rounding per stored population (the populations are re-read from L1)
-    asm volatile("" ::: "memory");
-    R rest = dl[C];
-    For<0, NP>::run([&]<int K>() {
-      constexpr int a = L::pfirst(K), b = L::opp(a);
-      const R oa = (R)fc[AA<Q>::template rd<a, PAR>(P, s)] + da[K];
-      const R ob = (R)fc[AA<Q>::template rd<b, PAR>(P, s)] + db[K];
+        da -= ev + od;
+        db -= ev - od;
+      }
+      const R oa = va + da;
+      const R ob = vb + db;
       if constexpr (sizeof(R) == 4) rest -= oa + ob;
-      store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<a, PAR>(P, s), oa);
-      store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<b, PAR>(P, s), ob);
+      store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<a, PAR>(P, so), oa);
+      store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<b, PAR>(P, so), ob);
     });
     // The weights rounded to FP32 sum to 1 + 7.5e-9 (D2Q9) or 1 + 1.5e-8 (D3Q19), which makes
     // every step scale the stored deviation rho_c - rho_ref_c by 1 + omega * that excess: a
@@ -442,9 +496,9 @@ struct FusedArgs {
   // plane-range form (k_fused3, D3Q19)
   int mode;                   // 1 (or 0): tile columns (k_fused), 3: plane ranges (k_fused3)
   const int* range;           // G + 1 range starts in the flattened (y, x) index of a plane
-  const int* nbr;             // G x kF3MaxNbr CTAs owning neighbour sites, -1 padded
+  const int* nbr;             // G x kF3MaxNbr workers owning neighbour sites, -1 padded
   void* psi_ring;             // (kF3Ring + 2) psi planes
-  int G, smax;                // CTAs, largest range
+  int G, smax;                // workers (two per CTA), largest range
 };
 
 constexpr unsigned kSpinLimit = 1u << 20;  // polls of one flag before giving up (~1 s)
@@ -891,8 +945,8 @@ struct Launch {
       Params Pc = P;
       FusedArgs Ac = A;
       void* args[] = {(void*)&Pc, (void*)&fp, (void*)&st, (void*)&t_dev, (void*)&Ac};
-      const size_t smem = (size_t)2 * (NC + 3) * A.smax * sizeof(R);
-      return cudaLaunchCooperativeKernel((const void*)k_fused3<NC, Prec, MRT>, dim3((unsigned)A.G),
+      const size_t smem = (size_t)2 * (kF3Lead + 1) * (NC + 3) * A.smax * sizeof(R);
+      return cudaLaunchCooperativeKernel((const void*)k_fused3<NC, Prec, MRT>, dim3((unsigned)(A.G / 2)),
                                          dim3(kF3Threads), args, smem, s);
     }
   }
