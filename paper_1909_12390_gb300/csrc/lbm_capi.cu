@@ -133,9 +133,45 @@ double w_q(int Q, int a) { return Q == 9 ? lbm::Lat<9>::w(a) : lbm::Lat<19>::w(a
 
 lbm_status ensure_scratch(lbm_ctx* c) {
   if (c->scratch) return LBM_OK;
-  size_t n = (size_t)(c->nc + 5) * (size_t)c->P.N;
+  size_t n = (size_t)(c->nc + 5) * (size_t)c->P.N + 8;  // fields, then 8 words for k_check_init
   CK(c, cudaMalloc(&c->scratch, n * sizeof(double)));
   return LBM_OK;
+}
+
+// Validation of lbm_init's inputs on the device (they are copied there anyway): out[s] =
+// smallest density of component s as its bit pattern (positive doubles order like their bits),
+// out[4] = smallest flat index of a density that is not finite and > 0, out[5] = 1 if some u
+// is not finite. out[0..4] start at all ones, out[5] at 0.
+__global__ void k_check_init(const double* __restrict__ rho, const double* __restrict__ u, long long N, int nc,
+                             unsigned long long* out) {
+  unsigned long long lo[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+  unsigned long long bad = ~0ull;
+  bool ubad = false;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)nc * N; i += stride) {
+    const double v = rho[i];
+    if (!(v > 0) || !isfinite(v)) {
+      bad = min(bad, (unsigned long long)i);
+    } else {
+      const int s = (int)(i / N);
+      const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k == s) lo[k] = min(lo[k], b);
+    }
+  }
+  if (u)
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * N; i += stride)
+      ubad = ubad || !isfinite(u[i]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    unsigned long long x = lo[k];
+    for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if ((threadIdx.x & 31) == 0 && k < nc && x != ~0ull) atomicMin(&out[k], x);
+  }
+  for (int o = 16; o > 0; o >>= 1) bad = min(bad, __shfl_xor_sync(0xffffffffu, bad, o));
+  if ((threadIdx.x & 31) == 0 && bad != ~0ull) atomicMin(&out[4], bad);
+  if (__any_sync(0xffffffffu, ubad) && (threadIdx.x & 31) == 0) atomicExch(&out[5], 1ull);
 }
 
 lbm_status sync_status(lbm_ctx* c) {
@@ -594,29 +630,36 @@ lbm_status lbm_init(lbm_ctx* c, const double* rho, const double* u) {
   if (!c) return LBM_ERR_ARG;
   if (!rho) return fail(c, LBM_ERR_ARG, "rho is NULL");
   const int64_t N = c->P.N;
-  double lo[4] = {0, 0, 0, 0};
-  for (int s = 0; s < c->nc; ++s) {
-    lo[s] = rho[s * N];
-    for (int64_t i = 0; i < N; ++i) {
-      double v = rho[s * N + i];
-      if (!(v > 0) || !std::isfinite(v)) return fail(c, LBM_ERR_ARG, "rho[%d][%lld] must be finite and > 0", s, (long long)i);
-      lo[s] = std::min(lo[s], v);
-    }
-  }
-  if (u)
-    for (int64_t i = 0; i < 3 * N; ++i)
-      if (!std::isfinite(u[i])) return fail(c, LBM_ERR_ARG, "u must be finite");
-  if (c->precision == LBM_FP32_SHIFTED && !c->ref_given) {
-    for (int s = 0; s < c->nc; ++s) c->P.rho_ref[s] = lo[s];
-    lbm::finalize_params(c->P);
-    drop_graph(c);  // the graph holds the parameters by value
-  }
   lbm_status st = ensure_scratch(c);
   if (st != LBM_OK) return st;
   double* d_rho = c->scratch;
   double* d_u = c->scratch + (size_t)c->nc * N;
+  unsigned long long* d_chk = (unsigned long long*)(c->scratch + (size_t)(c->nc + 5) * N);
   CK(c, cudaMemcpyAsync(d_rho, rho, (size_t)c->nc * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   if (u) CK(c, cudaMemcpyAsync(d_u, u, (size_t)3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  // densities finite and > 0, u finite, and the component minima (the default FP32 shift)
+  unsigned long long chk[6];
+  CK(c, cudaMemsetAsync(d_chk, 0xff, 5 * sizeof(unsigned long long), c->stream));
+  CK(c, cudaMemsetAsync(d_chk + 5, 0, sizeof(unsigned long long), c->stream));
+  const long long work = (long long)c->nc * N;
+  const unsigned nb = (unsigned)std::min<long long>((work + 255) / 256, 4096);
+  k_check_init<<<nb, 256, 0, c->stream>>>(d_rho, u ? d_u : nullptr, (long long)N, c->nc, d_chk);
+  CK(c, cudaGetLastError());
+  CK(c, cudaMemcpyAsync(chk, d_chk, sizeof chk, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (chk[4] != ~0ull)
+    return fail(c, LBM_ERR_ARG, "rho[%d][%lld] must be finite and > 0", (int)(chk[4] / (unsigned long long)N),
+                (long long)(chk[4] % (unsigned long long)N));
+  if (chk[5]) return fail(c, LBM_ERR_ARG, "u must be finite");
+  if (c->precision == LBM_FP32_SHIFTED && !c->ref_given) {
+    for (int s = 0; s < c->nc; ++s) {
+      double lo;
+      std::memcpy(&lo, &chk[s], sizeof lo);
+      c->P.rho_ref[s] = lo;
+    }
+    lbm::finalize_params(c->P);
+    drop_graph(c);  // the graph holds the parameters by value
+  }
   c->ops->init(c->P, c->f, d_rho, u ? d_u : nullptr, c->stream);
   CK(c, cudaGetLastError());
   CK(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
@@ -704,8 +747,9 @@ lbm_status lbm_fields(lbm_ctx* c, double* rho, double* u, double* p, double* psi
   double* d_p = d_u + (size_t)3 * N;
   double* d_psi = d_p + N;
   const int parity = (int)(c->t & 1);
-  c->ops->psi(c->P, c->f, c->psi, c->status, parity, c->stream);
-  c->ops->fields(c->P, c->f, c->psi, d_rho, d_u, d_p, d_psi, parity, c->stream);
+  if (u || psi) c->ops->psi(c->P, c->f, c->psi, c->status, parity, c->stream);  // the state's psi
+  c->ops->fields(c->P, c->f, c->psi, rho ? d_rho : nullptr, u ? d_u : nullptr, p ? d_p : nullptr,
+                 psi ? d_psi : nullptr, parity, c->stream);
   CK(c, cudaGetLastError());
   if (rho) CK(c, cudaMemcpyAsync(rho, d_rho, (size_t)c->nc * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   if (u) CK(c, cudaMemcpyAsync(u, d_u, (size_t)3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));

@@ -729,32 +729,44 @@ __global__ void __launch_bounds__(Fused<Q>::NT, Q == 19 ? 2 : 4)
 // ---------------------------------------------------------------------------------------
 // Set-up and read-back kernels (FP64 arithmetic, not on the timed path).
 
-// f = f_eq(rho_c, u) of Eq. equilibrium(a), stored in the even layout, shift subtracted.
+// f = f_eq(rho_c, u) of Eq. equilibrium(a), stored in the even layout, shift subtracted:
+// f - w_a rho_ref = w_a [(rho - rho_ref) + rho P_a], P_a = 3 e.u + 9/2 (e.u)^2 - 3/2 u.u. The
+// difference rho - rho_ref is taken in FP64; for FP32 storage the rest is FP32 arithmetic
+// (its result is rounded to FP32 anyway), for FP64 storage FP64.
 template <int Q, int NC, class Prec>
 __global__ void k_init(const Params P, typename Prec::S* f, const double* __restrict__ rho,
                        const double* __restrict__ u) {
   using L = Lat<Q>;
+  using R = typename Prec::R;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= P.N) return;
-  double uv[3] = {0, 0, 0}, uu = 0;
+  R uv[3] = {0, 0, 0}, uu = 0;
   if (u) {
 #pragma unroll
     for (int d = 0; d < L::D; ++d) {
-      uv[d] = u[d * P.N + idx];
+      uv[d] = (R)u[d * P.N + idx];
       uu += uv[d] * uv[d];
     }
+  }
+  R pa[Q];
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    R eu = 0;
+#pragma unroll
+    for (int d = 0; d < L::D; ++d) {
+      if (L::e(a, d) > 0) eu += uv[d];
+      if (L::e(a, d) < 0) eu -= uv[d];
+    }
+    pa[a] = eu * ((R)3 + (R)4.5 * eu) - (R)1.5 * uu;
   }
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     const double r = rho[c * P.N + idx];
+    const R dr = (R)(r - P.rho_ref[c]);
+    const R rr = (R)r;
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
-      double eu = 0;
-#pragma unroll
-      for (int d = 0; d < L::D; ++d) eu += L::e(a, d) * uv[d];
-      double feq = r * L::w(a) * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
-      f[((int64_t)c * Q + a) * P.N + idx] = (typename Prec::S)(feq - L::w(a) * P.rho_ref[c]);
-    }
+    for (int a = 0; a < Q; ++a)
+      f[((int64_t)c * Q + a) * P.N + idx] = (typename Prec::S)((R)L::w(a) * (dr + rr * pa[a]));
   }
 }
 
@@ -795,46 +807,49 @@ __global__ void k_set_f(const Params P, typename Prec::S* f, const double* __res
     }
 }
 
-// Macroscopic fields of the current state; psi must hold this state's pseudo-potential.
+// Macroscopic fields of the current state: component densities, barycentric velocity with the
+// Guo half force, EOS pressure and psi; each only when its output pointer is set (psi must hold
+// this state's pseudo-potential when u or psi is asked for). Moments and force in the storage
+// precision's arithmetic, the EOS in FP64, outputs FP64.
 template <int Q, int NC, class Prec, int PAR>
 __device__ __forceinline__ void fields_body(const Params& P, const typename Prec::S* __restrict__ f,
                                             const typename Prec::PsiT* __restrict__ psi, double* rho_out,
                                             double* u_out, double* p_out, double* psi_out, const Site& s) {
   using L = Lat<Q>;
+  using R = typename Prec::R;
   const int64_t idx = s.idx;
-  double rc[NC], j[3] = {0, 0, 0}, rho = 0;
-  For<0, NC>::run([&]<int C>() {
-    const typename Prec::S* fc = comp_base<Q>(f, P, C);
-    double acc = 0;
-    For<0, Q>::run([&]<int A>() {
-      double v = (double)fc[AA<Q>::template rd<A, PAR>(P, s)];
-      acc += v;
+  R dl[NC], j[3];
+  site_moments<Q, NC, Prec, PAR>(P, f, s, dl, j);
+  double rc[NC], rho = 0;
 #pragma unroll
-      for (int d = 0; d < L::D; ++d) j[d] += L::e(A, d) * v;
-    });
-    rc[C] = P.rho_ref[C] + acc;
-    rho += rc[C];
-  });
-  double s1[3] = {0, 0, 0}, s2[3] = {0, 0, 0};
-  For<1, Q>::run([&]<int A>() {
-    double pn = (double)psi[s.nb(P, L::e(A, 0), L::e(A, 1), L::e(A, 2))];
-#pragma unroll
-    for (int d = 0; d < L::D; ++d) {
-      s1[d] += L::w(A) * pn * L::e(A, d);
-      s2[d] += L::w(A) * pn * pn * L::e(A, d);
-    }
-  });
-  const double p0 = (double)psi[idx];
-  EosOut<NC> e = eos_pr<NC>(P, rc);
-#pragma unroll
-  for (int c = 0; c < NC; ++c)
+  for (int c = 0; c < NC; ++c) {
+    rc[c] = P.rho_ref[c] + (double)dl[c];
+    rho += rc[c];
     if (rho_out) rho_out[c * P.N + idx] = rc[c];
-  for (int d = 0; d < 3; ++d) {
-    double F = d < L::D ? -P.beta * P.G * p0 * s1[d] - 0.5 * (1.0 - P.beta) * P.G * s2[d] : 0.0;
-    if (u_out) u_out[d * P.N + idx] = (j[d] + 0.5 * F) / rho;
   }
-  if (p_out) p_out[idx] = e.pD / e.Dd;
-  if (psi_out) psi_out[idx] = p0;
+  if (u_out) {
+    R s1[3] = {0, 0, 0}, s2[3] = {0, 0, 0};
+    For<1, Q>::run([&]<int A>() {
+      const R pn = (R)psi[s.nb(P, L::e(A, 0), L::e(A, 1), L::e(A, 2))];
+#pragma unroll
+      for (int d = 0; d < L::D; ++d) {
+        if (L::e(A, d) != 0) {
+          s1[d] += (R)(L::w(A) * L::e(A, d)) * pn;
+          s2[d] += (R)(L::w(A) * L::e(A, d)) * pn * pn;
+        }
+      }
+    });
+    const R p0 = (R)psi[idx];
+    for (int d = 0; d < 3; ++d) {
+      const R F = d < L::D ? PC<R>::c1(P) * p0 * s1[d] + PC<R>::c2(P) * s2[d] : (R)0;
+      u_out[d * P.N + idx] = (double)((j[d] + (R)0.5 * F) / (R)rho);
+    }
+  }
+  if (p_out) {
+    EosOut<NC> e = eos_pr<NC>(P, rc);
+    p_out[idx] = e.pD / e.Dd;
+  }
+  if (psi_out) psi_out[idx] = (double)psi[idx];
 }
 
 template <int Q, int NC, class Prec>

@@ -299,3 +299,28 @@ def test_droplet_full_length_against_stored_oracle(cases):
     m = gpu.mass()
     assert np.all(np.abs(m / ref["droplet_mass"] - 1) < 1e-4)
     gpu.close()
+
+
+def test_init_rejects_bad_densities_and_velocities(cases):
+    """lbm_init checks its inputs on the device: the first density that is not finite and > 0
+    is named, a non-finite velocity is rejected, and a valid init afterwards works."""
+    from paper_1909_12390_gb300 import lbm
+    c = cases["c2"]
+    shape = (16, 8)
+    gpu = gpu_lattice(c, shape, FP32S)
+    rho = random_rho(c, tuple(reversed(shape)), seed=3)
+    bad = rho.copy()
+    bad[1, 5, 7] = -1.0
+    bad[2, 0, 1] = np.nan
+    with pytest.raises(lbm.LBMError) as ei:
+        gpu.init(bad)
+    assert ei.value.status == lbm.ERR_ARG and "rho[1][87]" in str(ei.value)
+    u = np.zeros((3,) + tuple(reversed(shape)))
+    u[0, 3, 3] = np.inf
+    with pytest.raises(lbm.LBMError) as ei:
+        gpu.init(rho, u)
+    assert ei.value.status == lbm.ERR_ARG and "u must be finite" in str(ei.value)
+    gpu.init(rho)
+    gpu.step(2)
+    assert gpu.time == 2
+    gpu.close()
