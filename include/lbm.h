@@ -266,6 +266,47 @@ lbm_status lbm_step_static(const lbm_grid *grid, int nc, const lbm_component *co
                            double tau, void *f_device, int64_t t0, int64_t n, void *stream, int64_t *t_out);
 const char *lbm_step_static_error(void);
 
+/* Batched two-phase flash (Section 3.2): the phase equilibrium of the Peng-Robinson mixture
+ * that sets up the multi-component runs of Section 4.2 (initial phase densities and the
+ * volatility coefficients gamma of Eq. gamma), for many (T, p, z) cases of one set of nc
+ * components, one GPU thread per case in FP64.
+ *
+ * comps: nc (1..4) components, Tc, pc, omega and M in any units consistent with the cases'
+ *   T and p (only T / Tc, p / pc and the ratios of M enter, except through R below);
+ * cases: ncase host structs: T, p, feed mole fractions z[0..nc) (each > 0, summing to 1),
+ *   kij[nc * nc] row-major symmetric binary interaction coefficients (zeta_ij);
+ * R: the gas constant in the units of p / (n T) (1 in lattice units);
+ * tol, maxit: successive substitution stops when max_i |d ln K_i| < tol (1e-13 reaches FP64
+ *   precision) or after maxit iterations;
+ * stream: a cudaStream_t (NULL = default stream); the call copies in, runs, copies out and
+ *   synchronises it; device memory is allocated and freed on the stream.
+ * out: ncase host structs. status 0: two phases, converged; 1: single phase or trivial
+ *   solution (K_i within 1e-4 of 1), only x = y = z, V, K and Z are meaningful; 2: two phases
+ *   not converged within maxit. V is the vapour mole fraction of the Rachford-Rice equation
+ *   (negative flash: it may leave [0, 1]); x, y the liquid and vapour mole fractions; Zl, Zv
+ *   the Gibbs-selected roots (Eq. solutionselection) of the PR cubic; residual Eq. error;
+ *   rho_l, rho_v the phase partial densities n x_i M_i with n = p / (Z R T); gamma the
+ *   per-component Eq. gamma, 1 for the least volatile component (smallest K).
+ * Returns LBM_ERR_ARG for invalid arguments (nothing runs) and LBM_ERR_CUDA for a CUDA
+ * failure; lbm_flash_error gives this thread's last message. */
+typedef struct {
+  double T, p;
+  double z[4];
+  double kij[16];
+} lbm_flash_case;
+typedef struct {
+  double V;
+  double x[4], y[4], K[4];
+  double Zl, Zv;
+  double residual;
+  double rho_l[4], rho_v[4], gamma[4];
+  int iterations;
+  int status;
+} lbm_flash_result;
+lbm_status lbm_flash(int nc, const lbm_component *comps, int ncase, const lbm_flash_case *cases, double R,
+                     double tol, int maxit, void *stream, lbm_flash_result *out);
+const char *lbm_flash_error(void);
+
 /* One-line description of the last failure of ctx ("" if none). Valid until the next call
  * on ctx. With ctx == NULL, the last failure of lbm_create. */
 const char *lbm_last_error(const lbm_ctx *ctx);

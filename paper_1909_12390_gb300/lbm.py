@@ -27,7 +27,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_init", "lbm_step"
            "lbm_step_static", "lbm_step_static_error", "lbm_batch_create", "lbm_batch_destroy",
            "lbm_batch_init", "lbm_batch_step", "lbm_batch_case_status", "lbm_batch_fields",
            "lbm_batch_get_f", "lbm_batch_tune", "lbm_batch_tune_report", "lbm_batch_sites",
-           "lbm_batch_last_error", "lbm_record", "lbm_adjoint")
+           "lbm_batch_last_error", "lbm_record", "lbm_adjoint", "lbm_flash", "lbm_flash_error")
 STATIC_MAX_SITES = 1048576
 PATH_AUTO, PATH_TWO_KERNEL, PATH_FUSED = 0, 1, 2
 FUSED_TILES, FUSED_PLANES = 1, 3
@@ -56,6 +56,21 @@ class Eos(ctypes.Structure):
                 ("beta", ctypes.c_double), ("G", ctypes.c_double), ("collision", ctypes.c_int),
                 ("mrt_rates", _DP), ("precision", ctypes.c_int), ("rho_ref", _DP)]
 
+
+class FlashCase(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_double), ("p", ctypes.c_double), ("z", ctypes.c_double * 4),
+                ("kij", ctypes.c_double * 16)]
+
+
+class FlashResult(ctypes.Structure):
+    _fields_ = [("V", ctypes.c_double), ("x", ctypes.c_double * 4), ("y", ctypes.c_double * 4),
+                ("K", ctypes.c_double * 4), ("Zl", ctypes.c_double), ("Zv", ctypes.c_double),
+                ("residual", ctypes.c_double), ("rho_l", ctypes.c_double * 4),
+                ("rho_v", ctypes.c_double * 4), ("gamma", ctypes.c_double * 4),
+                ("iterations", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+FLASH_TWO_PHASE, FLASH_SINGLE, FLASH_NOT_CONVERGED = 0, 1, 2
 
 _lib = None
 
@@ -95,6 +110,10 @@ def lib() -> ctypes.CDLL:
                                       ctypes.POINTER(Eos), ctypes.c_double, vp, ctypes.c_int64, ctypes.c_int64,
                                       vp, ctypes.POINTER(ctypes.c_int64)]
         L.lbm_step_static_error.argtypes = []
+        L.lbm_flash.argtypes = [ctypes.c_int, ctypes.POINTER(Component), ctypes.c_int, ctypes.POINTER(FlashCase),
+                                ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, ctypes.POINTER(FlashResult)]
+        L.lbm_flash_error.argtypes = []
+        L.lbm_flash_error.restype = ctypes.c_char_p
         L.lbm_step_static_error.restype = ctypes.c_char_p
         L.lbm_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(Grid), ctypes.c_int,
                                        ctypes.POINTER(Component), ctypes.POINTER(Eos), _DP, ctypes.POINTER(vp)]
@@ -170,6 +189,41 @@ def step_static(shape, components, T, tau, f_device_ptr: int, t0: int, n: int, s
     if st != OK:
         raise LBMError(st, lib().lbm_step_static_error().decode())
     return tout.value
+
+
+def flash(components, T, p, z, kij=None, R=1.0, tol=1e-13, maxit=20000, stream: int = 0):
+    """lbm_flash over the cases (T[k], p[k], z[k], kij[k]) of one set of components
+    ((Tc, pc, omega, M) tuples). T, p: (ncase,); z: (ncase, nc); kij: (ncase, nc, nc) or None.
+    Returns a dict of arrays: V, x, y, K, Zl, Zv, residual, rho_l, rho_v, gamma, iterations,
+    status (FLASH_TWO_PHASE, FLASH_SINGLE, FLASH_NOT_CONVERGED)."""
+    nc = len(components)
+    if not 1 <= nc <= 4:
+        raise LBMError(ERR_ARG, "nc must be 1..4")
+    T = np.atleast_1d(np.asarray(T, dtype=np.float64))
+    p = np.atleast_1d(np.asarray(p, dtype=np.float64))
+    z = np.asarray(z, dtype=np.float64).reshape(len(T), nc)
+    kij = np.zeros((len(T), nc, nc)) if kij is None else np.asarray(kij, dtype=np.float64).reshape(len(T), nc, nc)
+    n = len(T)
+    comps = (Component * nc)(*[Component(*map(float, c)) for c in components])
+    cases = (FlashCase * max(n, 1))()
+    for k in range(n):
+        cases[k].T, cases[k].p = T[k], p[k]
+        for i in range(nc):
+            cases[k].z[i] = z[k, i]
+            for j in range(nc):
+                cases[k].kij[i * nc + j] = kij[k, i, j]
+    out = (FlashResult * max(n, 1))()
+    st = lib().lbm_flash(nc, comps, n, cases, float(R), float(tol), int(maxit), ctypes.c_void_p(stream or None), out)
+    if st != OK:
+        raise LBMError(st, lib().lbm_flash_error().decode())
+    res = {}
+    for name in ("V", "Zl", "Zv", "residual"):
+        res[name] = np.array([getattr(out[k], name) for k in range(n)])
+    for name in ("x", "y", "K", "rho_l", "rho_v", "gamma"):
+        res[name] = np.array([list(getattr(out[k], name))[:nc] for k in range(n)]).reshape(n, nc)
+    res["iterations"] = np.array([out[k].iterations for k in range(n)])
+    res["status"] = np.array([out[k].status for k in range(n)])
+    return res
 
 
 class Lattice:

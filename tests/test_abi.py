@@ -3,6 +3,7 @@ declares; host-side argument validation and the Section 4.2 unit scaling (no GPU
 import os
 import re
 
+import numpy as np
 import pytest
 
 from conftest import ROOT
@@ -78,3 +79,23 @@ def test_scale_to_lattice_matches_section_4_2(lib):
         assert g[3] == pytest.approx(w.M, rel=1e-14)
     assert T == pytest.approx(666.06 * ts, rel=1e-14)
     assert p == pytest.approx(200.0 * ps, rel=1e-14)
+
+
+def test_flash_rejects_bad_arguments_before_any_device_work():
+    """lbm_flash validates on the host and returns LBM_ERR_ARG without touching the GPU."""
+    from paper_1909_12390_gb300 import lbm
+    comps = [(0.0729, 0.0596, 0.011, 1.0), (0.163, 0.049, 0.2, 3.62)]
+    bad = [
+        dict(T=[0.1], p=[0.05], z=[[0.5, 0.6]]),                      # z does not sum to 1
+        dict(T=[-0.1], p=[0.05], z=[[0.5, 0.5]]),                     # T <= 0
+        dict(T=[0.1], p=[0.05], z=[[0.5, 0.5]], kij=[[[0, 0.1], [0.2, 0]]]),  # asymmetric
+    ]
+    for kw in bad:
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.flash(comps, **kw)
+        assert ei.value.status == lbm.ERR_ARG
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.flash(comps * 3, [0.1], [0.05], [[1.0 / 6] * 6])          # nc > 4
+    assert ei.value.status == lbm.ERR_ARG
+    r = lbm.flash(comps, [], [], np.zeros((0, 2)))                     # no cases: nothing to do
+    assert r["V"].shape == (0,)
