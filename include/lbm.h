@@ -90,7 +90,17 @@ typedef struct {
                               vapour value of a two-phase field: vapour populations are then
                               stored as small deviations, liquid ones at FP32's relative
                               precision) */
+  int split;               /* force split factor: LBM_SPLIT_VOLATILITY (0), the paper's
+                              chi_i = gamma_i rho_i / sum_j gamma_j rho_j (Eq. distributionforce);
+                              or LBM_SPLIT_GONG (1), the comparison model of Eq. Gong with the
+                              two pressures under the root in the order that makes their
+                              difference non-negative (the paper swaps them to keep the root
+                              real, Section 4.2): chi_i = c_i sqrt(|p0 - ph_i|) / sum_j
+                              c_j sqrt(|p0 - ph_j|), c_i the molar composition, ph_i the PR
+                              pressure of pure i at the mixture's molar density n, p0 = n R T;
+                              evaluated in FP64. gamma is ignored with LBM_SPLIT_GONG. */
 } lbm_eos;
+enum { LBM_SPLIT_VOLATILITY = 0, LBM_SPLIT_GONG = 1 };
 
 /* Creates a context for one periodic lattice with nc components (1..4), relaxation time
  * tau > 1/2 (Eq. LBE). Validates every argument (LBM_ERR_ARG) and allocates the device

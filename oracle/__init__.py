@@ -46,7 +46,7 @@ class _Case(ctypes.Structure):
                 ("Tc", ctypes.c_double * 4), ("pc", ctypes.c_double * 4),
                 ("omega", ctypes.c_double * 4), ("M", ctypes.c_double * 4),
                 ("kij", ctypes.c_double * 16), ("gamma", ctypes.c_double * 4),
-                ("beta", ctypes.c_double), ("G", ctypes.c_double)]
+                ("beta", ctypes.c_double), ("G", ctypes.c_double), ("split", ctypes.c_int)]
 
 
 _lib = None
@@ -102,6 +102,7 @@ class Case:
     R: float = 1.0
     collision: int = 0
     s: list = None
+    split: int = 0  # 0: Eq. distributionforce; 1: Eq. Gong with sqrt(|p0 - ph_i|)
 
     def __post_init__(self):
         nc = len(self.Tc)
@@ -137,6 +138,7 @@ class Case:
             for k, v in enumerate(self.s):
                 c.s[k] = v
         c.T, c.R = self.T, self.R
+        c.split = self.split
         for i in range(self.nc):
             c.Tc[i], c.pc[i], c.omega[i], c.M[i] = self.Tc[i], self.pc[i], self.omega[i], self.M[i]
             c.gamma[i] = self.gamma[i]

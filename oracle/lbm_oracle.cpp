@@ -40,6 +40,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 namespace {
@@ -199,6 +200,7 @@ typedef struct {
   double kij[16];  // binary interaction coefficients zeta_ij, row-major nc x nc
   double gamma[4]; // volatility coefficients gamma_i of Eq. distributionforce
   double beta, G;  // Kupershtokh beta and interaction strength (Eq. coupledMCforce)
+  int split;       // 0: Eq. distributionforce (gamma); 1: Eq. Gong, |p0 - ph_i| (FP64 only)
 } oracle_case;
 
 enum { ORACLE_OK = 0, ORACLE_ERR_ARG = -1, ORACLE_ERR_PSI_DOMAIN = -4, ORACLE_ERR_NONFINITE = -5 };
@@ -217,6 +219,7 @@ struct Setup {
   double Mm[19 * 19], Minv[19 * 19];
   double RT, G, beta;
   double aalpha[4], b[4], M[4];
+  int split;
 };
 
 // a_i, b_i, alpha_i(T), m_i of Section 3.2 (Eq. SCpengrobinson's mixture counterpart).
@@ -243,6 +246,8 @@ int make_setup(const oracle_case* c, Setup* S) {
   S->N = (int64_t)c->nx * c->ny * c->nz;
   S->tau = c->tau;
   S->collision = c->collision;
+  if (c->split != 0 && c->split != 1) return ORACLE_ERR_ARG;
+  S->split = c->split;
   for (int k = 0; k < 19; ++k) S->s[k] = c->s[k];
   S->RT = c->R * c->T;
   S->G = c->G;
@@ -393,9 +398,30 @@ int step_once(const Setup& S, const T* kij, const T* gamma, const T* fin, T* fou
     }
     T uu = 0.0;
     for (int d = 0; d < D; ++d) uu += u[d] * u[d];
+    // Gong et al.'s split (Eq. Gong) with the two pressures under the root put in the order
+    // that makes the difference non-negative, as the paper does to keep it real (Section
+    // 4.2): chi_i = c_i sqrt(|p0 - ph_i|) / sum_j (...), c_i the molar composition, ph_i the
+    // PR pressure of pure i at the mixture's molar density n, p0 = n R T.
+    double gong[4] = {0, 0, 0, 0};
+    if (S.split == 1) {
+      if constexpr (std::is_same_v<T, double>) {
+        double nmol[4], nt = 0.0, wsum = 0.0;
+        for (int s = 0; s < nc; ++s) {
+          nmol[s] = m.rho_c[s * N + x] / S.M[s];
+          nt += nmol[s];
+        }
+        const double p0 = nt * S.RT;
+        for (int s = 0; s < nc; ++s) {
+          const double b = S.b[s], ph = p0 / (1.0 - b * nt) - S.aalpha[s] * nt * nt / (1.0 + 2.0 * b * nt - b * b * nt * nt);
+          gong[s] = nmol[s] / nt * std::sqrt(std::fabs(p0 - ph));
+          wsum += gong[s];
+        }
+        for (int s = 0; s < nc; ++s) gong[s] /= wsum;
+      }
+    }
     for (int s = 0; s < nc; ++s) {
       T rs = m.rho_c[s * N + x];
-      T chi = gamma[s] * rs / gsum;  // Eq. distributionforce
+      T chi = S.split == 1 ? T(gong[s]) : gamma[s] * rs / gsum;  // Eq. Gong / Eq. distributionforce
       T Fs[3] = {chi * Fx[0], chi * Fx[1], chi * Fx[2]};
       T feq[19], fbar[19], fa[19];
       for (int a = 0; a < Q; ++a) {
@@ -487,6 +513,7 @@ int oracle_step_dual(const oracle_case* c, const double* dkij, const double* dga
   Setup S;
   int st = make_setup(c, &S);
   if (st != ORACLE_OK) return st;
+  if (S.split != 0) return ORACLE_ERR_ARG;  // the dual path differentiates Eq. distributionforce
   const int nc = S.nc;
   const size_t n = (size_t)nc * S.L.Q * S.N;
   Dual kij[16], gamma[4];

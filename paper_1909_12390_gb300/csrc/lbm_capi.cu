@@ -459,6 +459,7 @@ lbm_status make_params(const lbm_grid* grid, int nc, const lbm_component* comps,
   if (!(eos->T > 0) || !std::isfinite(eos->T)) return bad("T must be > 0");
   if (!(eos->G != 0) || !std::isfinite(eos->G)) return bad("G must be nonzero");
   if (!std::isfinite(eos->beta)) return bad("beta must be finite");
+  if (eos->split != LBM_SPLIT_VOLATILITY && eos->split != LBM_SPLIT_GONG) return bad("split must be 0 or 1");
   const double R = eos->R == 0 ? 1.0 : eos->R;
   if (!(R > 0) || !std::isfinite(R)) return bad("R must be > 0");
   for (int i = 0; i < nc; ++i) {
@@ -520,6 +521,7 @@ lbm_status make_params(const lbm_grid* grid, int nc, const lbm_component* comps,
   P.RT = R * eos->T;
   P.cpsi = 2.0 / (eos->G * (1.0 / 3.0));
   P.beta = eos->beta;
+  P.split = eos->split;
   P.G = eos->G;
   finalize_params(P);
   *ops_out = ops;
@@ -838,6 +840,8 @@ lbm_status lbm_restore(lbm_ctx* c, const void* buf, size_t bytes, int64_t t) {
 lbm_status lbm_record(lbm_ctx* c, int64_t n, int checkpoint_every) {
   if (!c) return LBM_ERR_ARG;
   if (c->collision != LBM_BGK) return fail(c, LBM_ERR_ARG, "the adjoint covers the BGK collision only");
+  if (c->P.split != LBM_SPLIT_VOLATILITY)
+    return fail(c, LBM_ERR_ARG, "the adjoint covers the volatility split (Eq. distributionforce) only");
   if (n < 1 || checkpoint_every < 1) return fail(c, LBM_ERR_ARG, "n and checkpoint_every must be >= 1");
   for (void* p : c->ckpt) cudaFree(p);
   c->ckpt.clear();

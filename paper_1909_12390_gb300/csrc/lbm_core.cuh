@@ -180,6 +180,7 @@ struct Params {
   double rho_ref[4]; // FP32 shift references (0 for FP64 storage)
   double gamma[4];
   double beta, G;
+  int split;          // LBM_SPLIT_VOLATILITY (0) or LBM_SPLIT_GONG (1)
   // constants derived by finalize_params(), in both precisions, so that no kernel converts a
   // parameter per site (an FP64 -> FP32 conversion runs on GB300's 1/72-rate FP64 pipe)
   double gk, c1, c2;  // 1 - omega/2, -beta G, -(1 - beta) G / 2

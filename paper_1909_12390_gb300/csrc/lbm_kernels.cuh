@@ -149,6 +149,31 @@ __device__ __forceinline__ double ld_pop(const double* p) {
   return v;
 }
 
+// Split factors of Gong et al.'s comparison model (Eq. Gong) with the two pressures under the
+// root put in the order that makes the difference non-negative, as the paper does to keep it
+// real (Section 4.2): chi_i = c_i sqrt(|p0 - ph_i|) / sum_j c_j sqrt(|p0 - ph_j|), c_i the
+// molar composition, ph_i the Peng-Robinson pressure of pure component i at the mixture's
+// molar density n, p0 = n R T. FP64 (the pressures cancel).
+template <int NC, class R>
+__device__ __forceinline__ void gong_split(const Params& P, const R (&rc)[NC], R (&chi)[NC]) {
+  double n[NC], nt = 0.0, w[NC], ws = 0.0;
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    n[i] = (double)rc[i] * P.invM[i];
+    nt += n[i];
+  }
+  const double p0 = nt * P.RT;
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    const double bn = P.b[i] * nt;
+    const double ph = p0 / (1.0 - bn) - P.sa[i] * P.sa[i] * nt * nt / (1.0 + bn * (2.0 - bn));
+    w[i] = n[i] / nt * sqrt(fabs(p0 - ph));
+    ws += w[i];
+  }
+#pragma unroll
+  for (int i = 0; i < NC; ++i) chi[i] = (R)(w[i] / ws);
+}
+
 // S1 moments of one site: shifted component densities dl_c = sum_a f_ca = rho_c - rho_ref_c
 // and the total momentum j = sum_c sum_a e_a f_ca. The momentum is summed from the differences
 // of opposite populations: near equilibrium the two are close, so in FP32 each difference is
@@ -265,12 +290,20 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
   const R F0 = -(R)(3.0 * L::w(0)) * uF;
   const R om = PC<R>::omega(P);
   const R gk = PC<R>::gk(P);
-  const R igs = (R)1 / gs;
+  // S5: split factors
+  R chis[NC];
+  if (P.split == 0) {
+    const R igs = (R)1 / gs;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) chis[c] = PC<R>::gamma(P, c) * rc[c] * igs;  // Eq. distributionforce
+  } else {
+    gong_split<NC, R>(P, rc, chis);
+  }
   For<0, NC>::run([&]<int C>() {
     // Compiler-only barrier: the populations are re-read (from L1) rather than kept in
     // registers from the moments pass, which would cost Q * NC registers.
     asm volatile("" ::: "memory");
-    const R chi = PC<R>::gamma(P, C) * rc[C] * igs;  // S5
+    const R chi = chis[C];
     const R gkchi = gk * chi;
     typename Prec::S* fc = comp_base<Q>(f, P, C);
     // Non-equilibrium part g = f - f_eq (stored variables) per pair: A is the even part of the

@@ -31,6 +31,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_init", "lbm_step"
 STATIC_MAX_SITES = 1048576
 PATH_AUTO, PATH_TWO_KERNEL, PATH_FUSED = 0, 1, 2
 FUSED_TILES, FUSED_PLANES = 1, 3
+SPLIT_VOLATILITY, SPLIT_GONG = 0, 1
 
 
 class LBMError(RuntimeError):
@@ -54,7 +55,7 @@ _DP = ctypes.POINTER(ctypes.c_double)
 class Eos(ctypes.Structure):
     _fields_ = [("T", ctypes.c_double), ("R", ctypes.c_double), ("kij", _DP), ("gamma", _DP),
                 ("beta", ctypes.c_double), ("G", ctypes.c_double), ("collision", ctypes.c_int),
-                ("mrt_rates", _DP), ("precision", ctypes.c_int), ("rho_ref", _DP)]
+                ("mrt_rates", _DP), ("precision", ctypes.c_int), ("rho_ref", _DP), ("split", ctypes.c_int)]
 
 
 class FlashCase(ctypes.Structure):
@@ -155,7 +156,7 @@ def _f64(a, n=None):
 
 
 def make_args(shape, components, T, gamma=None, kij=None, beta=1.0, G=-1.0, collision=BGK,
-              mrt_rates=None, precision=FP64, rho_ref=None, R=1.0):
+              mrt_rates=None, precision=FP64, rho_ref=None, R=1.0, split=0):
     """The lbm_grid, lbm_component[] and lbm_eos of one lattice (plus arrays to keep alive)."""
     shape = tuple(int(s) for s in shape)
     Q = D2Q9 if len(shape) == 2 else D3Q19
@@ -174,7 +175,7 @@ def make_args(shape, components, T, gamma=None, kij=None, beta=1.0, G=-1.0, coll
 
     eos = Eos(T=T, R=R, kij=arr(None if kij is None else np.asarray(kij, dtype=float).ravel(), nc * nc),
               gamma=arr(gamma, nc), beta=beta, G=G, collision=collision,
-              mrt_rates=arr(mrt_rates, Q), precision=precision, rho_ref=arr(rho_ref, nc))
+              mrt_rates=arr(mrt_rates, Q), precision=precision, rho_ref=arr(rho_ref, nc), split=int(split))
     return Grid(nx, ny, nz, Q), comps, eos, keep
 
 
@@ -233,11 +234,11 @@ class Lattice:
     shape (nc, nz, ny, nx) / (nc, ny, nx) (x fastest), populations as (nc, Q, *grid)."""
 
     def __init__(self, shape, components, T, tau, gamma=None, kij=None, beta=1.0, G=-1.0,
-                 collision=BGK, mrt_rates=None, precision=FP64, rho_ref=None, R=1.0):
+                 collision=BGK, mrt_rates=None, precision=FP64, rho_ref=None, R=1.0, split=0):
         L = lib()
         grid, comps, eos, keep = make_args(shape, components, T, gamma=gamma, kij=kij, beta=beta, G=G,
                                            collision=collision, mrt_rates=mrt_rates, precision=precision,
-                                           rho_ref=rho_ref, R=R)
+                                           rho_ref=rho_ref, R=R, split=split)
         self._keep = keep
         shape = tuple(int(s) for s in shape)
         self.Q = grid.lattice
@@ -389,7 +390,7 @@ class Batch:
             g, cp, e, keep = make_args(c["shape"], c["components"], c["T"], gamma=c.get("gamma"),
                                        kij=c.get("kij"), beta=c.get("beta", 1.0), G=c.get("G", -1.0),
                                        collision=collision, mrt_rates=c.get("mrt_rates"),
-                                       precision=precision, rho_ref=c.get("rho_ref"))
+                                       precision=precision, rho_ref=c.get("rho_ref"), split=c.get("split", 0))
             grids[i] = g
             for k in range(nc):
                 comps[i * nc + k] = cp[k]

@@ -469,3 +469,33 @@ def test_flat_interface_honours_iso_fugacity(p_psia):
     assert abs(r["y1"] / fr.y[0] - 1) < 0.040
     assert abs(r["rho_l"] / r["rl"] - 1) < 0.021
     assert abs(r["rho_v"] / r["rv"] - 1) < 0.021
+
+
+def test_gong_split_of_identical_components_reduces_to_the_composition():
+    """For two identical components the pure-component pressures in Eq. Gong are equal, so
+    the split factor is the molar composition c_i; with equal molar masses that is
+    rho_i / rho, the volatility split of Eq. distributionforce with gamma = 1. One step of
+    each must agree to rounding."""
+    c = {r[0]: th.Component(r[0], r[2], r[1], r[3], r[4]) for r in read_table("table1_components.txt")}
+    lb, ts, _ = th.lattice_components([c["C3"], c["C3"]])
+    T = 0.9 * lb[0].Tc
+    base = dict(Q=9, shape=(12, 10), Tc=[k.Tc for k in lb], pc=[k.pc for k in lb],
+                omega=[k.omega for k in lb], M=[k.M for k in lb], T=T, tau=0.8, gamma=[1.0, 1.0],
+                beta=1.5, G=-1.0)
+    grid = (10, 12)
+    u = lbm_inputs.uniform01(21, 2 * 120).reshape((2,) + grid)
+    rho = 0.5 + 4.0 * u
+    a = oracle.Case(**base, split=0)
+    b = oracle.Case(**base, split=1)
+    fa = oracle.step(a, oracle.equilibrium(a, rho), 3)
+    fb = oracle.step(b, oracle.equilibrium(b, rho), 3)
+    assert np.max(np.abs(fa - fb)) < 1e-12 * np.max(np.abs(fa))
+    # and the split is not trivially the volatility one when the components differ
+    lb2, _, _ = th.lattice_components([c["C3"], c["nC5"]])
+    base2 = dict(base, Tc=[k.Tc for k in lb2], pc=[k.pc for k in lb2], omega=[k.omega for k in lb2],
+                 M=[k.M for k in lb2])
+    a2 = oracle.Case(**base2, split=0)
+    b2 = oracle.Case(**base2, split=1)
+    fa2 = oracle.step(a2, oracle.equilibrium(a2, rho), 3)
+    fb2 = oracle.step(b2, oracle.equilibrium(b2, rho), 3)
+    assert np.max(np.abs(fa2 - fb2)) > 1e-6 * np.max(np.abs(fa2))
