@@ -125,7 +125,12 @@ def test_plain_shan_chen_force_fails_cleanly_at_the_flat_interface_state(split):
     with pytest.raises(lbm.LBMError) as ei:
         gpu.step(2000)
     assert ei.value.status in (lbm.ERR_NONFINITE, lbm.ERR_PSI_DOMAIN)
-    assert 0 < gpu.time < 2000
+    ocase = oracle.Case(Q=9, shape=(400, 2), Tc=[k.Tc for k in lb], pc=[k.pc for k in lb],
+                        omega=[k.omega for k in lb], M=[k.M for k in lb], T=T, tau=0.8, gamma=g, beta=1.0,
+                        G=-1.0, split=split)
+    with pytest.raises(oracle.OracleError) as eo:
+        oracle.step(ocase, oracle.equilibrium(ocase, rho), 2000)
+    assert abs(gpu.time - eo.value.step) <= 2, (gpu.time, eo.value.step)
     gpu.init(rho)
     gpu.step(5)
     assert gpu.time == 5
