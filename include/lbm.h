@@ -317,6 +317,33 @@ lbm_status lbm_flash(int nc, const lbm_component *comps, int ncase, const lbm_fl
                      double tol, int maxit, void *stream, lbm_flash_result *out);
 const char *lbm_flash_error(void);
 
+/* Diagnostics of the current state (the checks of Sections 4.2 and 4.3), computed on the
+ * device from the component densities and the EOS pressure of every site:
+ *   * the contour level: params->threshold if > 0, else (rho_max + rho_min) / 2 of the total
+ *     density rho = sum_s rho_s;
+ *   * the bulk phases: cells whose whole (2 erode + 1)^D box (periodic) lies above the level
+ *     (liquid) or below it (vapour), i.e. farther than `erode` cells from the contour in the
+ *     L-infinity norm (the paper's bulk cells are those more than 8 cells from the contour);
+ *   * their mean component densities rho_l / rho_v, EOS pressures p_l / p_v, molar
+ *     compositions x / y and the iso-fugacity residual of Eq. error with f_i = phi_i c_i p,
+ *     ln phi_i from Eq. fugacitycoeff2 at Z = p / (n R T) (no cubic solve);
+ *   * liquid_cells (cells above the level), the equivalent radius sqrt(cells / pi) in 2-D or
+ *     cbrt(3 cells / (4 pi)) in 3-D, and dp = p_l - p_v (Laplace's law: dp = sigma / R in 2-D).
+ * Sums use FP64 atomics (their order is not fixed: results agree to rounding between calls).
+ * Allocates and frees a device work buffer of ~12 bytes per site on the context's stream;
+ * synchronises it. NaN where a phase has no bulk cell. */
+typedef struct {
+  double threshold;  /* contour level of the total density; <= 0: (rho_max + rho_min) / 2 */
+  int erode;         /* bulk cells are farther than this from the contour (>= 0) */
+} lbm_diag_params;
+typedef struct {
+  double threshold, rho_max, rho_min;
+  double rho_l[4], rho_v[4], p_l, p_v, x[4], y[4];
+  double residual, radius, dp;
+  int64_t n_l, n_v, liquid_cells;
+} lbm_diag_result;
+lbm_status lbm_diagnostics(lbm_ctx *ctx, const lbm_diag_params *params, lbm_diag_result *out);
+
 /* One-line description of the last failure of ctx ("" if none). Valid until the next call
  * on ctx. With ctx == NULL, the last failure of lbm_create. */
 const char *lbm_last_error(const lbm_ctx *ctx);

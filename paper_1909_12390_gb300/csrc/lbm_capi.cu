@@ -763,6 +763,28 @@ lbm_status lbm_fields(lbm_ctx* c, double* rho, double* u, double* p, double* psi
   return st;
 }
 
+lbm_status lbm_diagnostics(lbm_ctx* c, const lbm_diag_params* dp, lbm_diag_result* out) {
+  if (!c) return LBM_ERR_ARG;
+  if (!dp || !out) return fail(c, LBM_ERR_ARG, "params and out must be non-NULL");
+  if (dp->erode < 0 || !std::isfinite(dp->threshold)) return fail(c, LBM_ERR_ARG, "erode must be >= 0 and threshold finite");
+  lbm_status st = ensure_scratch(c);
+  if (st != LBM_OK) return st;
+  const int64_t N = c->P.N;
+  double* d_rho = c->scratch;
+  double* d_p = d_rho + (size_t)(c->nc + 3) * N;
+  c->ops->fields(c->P, c->f, c->psi, d_rho, nullptr, d_p, nullptr, (int)(c->t & 1), c->stream);
+  CK(c, cudaGetLastError());
+  void* work = nullptr;
+  CK(c, cudaMallocAsync(&work, (size_t)12 * N + 256, c->stream));
+  std::string why;
+  st = lbm::diagnostics(c->P, c->nc, c->Q == 19 ? 3 : 2, dp, d_rho, d_p, work, c->stream, out, &why);
+  cudaFreeAsync(work, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (st != LBM_OK) return fail(c, st, "diagnostics: %s", why.c_str());
+  CK(c, e);
+  return LBM_OK;
+}
+
 lbm_status lbm_mass(lbm_ctx* c, double* mass) {
   if (!c || !mass) return c ? fail(c, LBM_ERR_ARG, "mass is NULL") : LBM_ERR_ARG;
   c->ops->mass(c->P, c->f, c->partial, c->mass_dev, c->stream);

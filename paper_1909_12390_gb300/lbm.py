@@ -27,7 +27,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_init", "lbm_step"
            "lbm_step_static", "lbm_step_static_error", "lbm_batch_create", "lbm_batch_destroy",
            "lbm_batch_init", "lbm_batch_step", "lbm_batch_case_status", "lbm_batch_fields",
            "lbm_batch_get_f", "lbm_batch_tune", "lbm_batch_tune_report", "lbm_batch_sites",
-           "lbm_batch_last_error", "lbm_record", "lbm_adjoint", "lbm_flash", "lbm_flash_error")
+           "lbm_batch_last_error", "lbm_record", "lbm_adjoint", "lbm_flash", "lbm_flash_error", "lbm_diagnostics")
 STATIC_MAX_SITES = 1048576
 PATH_AUTO, PATH_TWO_KERNEL, PATH_FUSED = 0, 1, 2
 FUSED_TILES, FUSED_PLANES = 1, 3
@@ -73,6 +73,18 @@ class FlashResult(ctypes.Structure):
 
 FLASH_TWO_PHASE, FLASH_SINGLE, FLASH_NOT_CONVERGED = 0, 1, 2
 
+
+class DiagParams(ctypes.Structure):
+    _fields_ = [("threshold", ctypes.c_double), ("erode", ctypes.c_int)]
+
+
+class DiagResult(ctypes.Structure):
+    _fields_ = [("threshold", ctypes.c_double), ("rho_max", ctypes.c_double), ("rho_min", ctypes.c_double),
+                ("rho_l", ctypes.c_double * 4), ("rho_v", ctypes.c_double * 4), ("p_l", ctypes.c_double),
+                ("p_v", ctypes.c_double), ("x", ctypes.c_double * 4), ("y", ctypes.c_double * 4),
+                ("residual", ctypes.c_double), ("radius", ctypes.c_double), ("dp", ctypes.c_double),
+                ("n_l", ctypes.c_int64), ("n_v", ctypes.c_int64), ("liquid_cells", ctypes.c_int64)]
+
 _lib = None
 
 
@@ -113,6 +125,7 @@ def lib() -> ctypes.CDLL:
         L.lbm_step_static_error.argtypes = []
         L.lbm_flash.argtypes = [ctypes.c_int, ctypes.POINTER(Component), ctypes.c_int, ctypes.POINTER(FlashCase),
                                 ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, ctypes.POINTER(FlashResult)]
+        L.lbm_diagnostics.argtypes = [vp, ctypes.POINTER(DiagParams), ctypes.POINTER(DiagResult)]
         L.lbm_flash_error.argtypes = []
         L.lbm_flash_error.restype = ctypes.c_char_p
         L.lbm_step_static_error.restype = ctypes.c_char_p
@@ -302,6 +315,18 @@ class Lattice:
     def fields_into(self, rho=None, u=None, p=None, psi=None):
         """Writes the fields into caller-provided C-contiguous float64 host arrays."""
         self._check(lib().lbm_fields(self._h, _dp(rho), _dp(u), _dp(p), _dp(psi)))
+
+    def diagnostics(self, erode: int = 8, threshold: float = 0.0) -> dict:
+        """lbm_diagnostics: bulk phases, compositions, iso-fugacity residual, radius, Laplace
+        jump of the current state (see include/lbm.h)."""
+        r = DiagResult()
+        self._check(lib().lbm_diagnostics(self._h, ctypes.byref(DiagParams(float(threshold), int(erode))),
+                                          ctypes.byref(r)))
+        out = {k: getattr(r, k) for k in ("threshold", "rho_max", "rho_min", "p_l", "p_v", "residual", "radius",
+                                          "dp", "n_l", "n_v", "liquid_cells")}
+        for k in ("rho_l", "rho_v", "x", "y"):
+            out[k] = np.array(list(getattr(r, k))[:self.nc])
+        return out
 
     def mass(self) -> np.ndarray:
         m = np.empty(self.nc)

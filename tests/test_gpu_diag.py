@@ -1,0 +1,96 @@
+"""lbm_diagnostics (device-side bulk phases, compositions, iso-fugacity residual, radius and
+Laplace jump) against the diagnostics oracle on the same states, and on the Section 4.2 flat
+interface against the flash."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import lbm_inputs
+import oracle
+from conftest import GOLDEN, read_table
+from lbm_cases import comps_of, gpu_lattice, oracle_case
+from oracle import diagnostics as dg
+from oracle import thermo as th
+
+pytestmark = pytest.mark.gpu
+
+FP64, FP32S = 0, 1
+
+
+@pytest.fixture(scope="module")
+def cases():
+    with open(os.path.join(GOLDEN, "cases.json")) as fh:
+        return json.load(fh)
+
+
+def _thermo_comps(c):
+    return [th.Component("c%d" % i, *k) for i, k in enumerate(comps_of(c))]
+
+
+def _compare(g, o, tol, count_tol=0):
+    assert g["threshold"] == pytest.approx(o["threshold"], rel=tol)
+    for k in ("n_l", "n_v", "liquid_cells"):
+        assert abs(g[k] - o[k]) <= count_tol * max(o[k], 1), (k, g[k], o[k])
+    for k in ("rho_l", "rho_v", "x", "y"):
+        assert np.allclose(g[k], o[k], rtol=tol, atol=0), (k, g[k], o[k])
+    for k in ("p_l", "p_v"):
+        assert g[k] == pytest.approx(o[k], rel=tol), k
+    assert g["radius"] == pytest.approx(o["radius"], rel=max(tol, count_tol))
+    assert g["residual"] == pytest.approx(o["residual"], rel=max(1e-6, 100 * tol), abs=1e-14)
+
+
+@pytest.mark.parametrize("shape,key,steps", [((96, 96), "c2", 150), ((32, 32, 32), "c3", 20)])
+@pytest.mark.parametrize("precision", [FP64, FP32S])
+def test_diagnostics_match_oracle(cases, shape, key, steps, precision):
+    """A droplet (D2Q9 MRT, three components) and a sphere (D3Q19 MRT), run on both sides; the
+    GPU diagnostics of the GPU state against the oracle diagnostics of the oracle state."""
+    c = cases[key]
+    radius = min(shape) / 4.0
+    grid = tuple(reversed(shape))
+    rho0 = lbm_inputs.ball_fields(grid, c["rho_l"], c["rho_v"], radius, 4.0)
+    ocase = oracle_case(c, shape)
+    f = oracle.step(ocase, oracle.equilibrium(ocase, rho0), steps)
+    fo = oracle.fields(ocase, f)
+    o = dg.bulk_diagnostics(_thermo_comps(c), c["kij"], c["T"], 1.0, fo.rho, fo.p, erode=max(2, min(8, int(radius / 3))))
+    gpu = gpu_lattice(c, shape, precision)
+    gpu.init(rho0)
+    gpu.step(steps)
+    g = gpu.diagnostics(erode=max(2, min(8, int(radius / 3))))
+    gpu.close()
+    if precision == FP64:
+        _compare(g, o, 1e-10)
+    else:
+        _compare(g, o, 2e-4, count_tol=0.02)
+
+
+def test_flat_interface_diagnostics_against_the_flash():
+    """Section 4.2 (C3/nC5 at 200 psia, 400 x 2, beta = 1.945, FP64, 14000 steps): the bulk
+    compositions and densities from lbm_diagnostics within the paper's reported accuracy of
+    the flash (4.0 % composition, 2.1 % density, Section 4.2), and the iso-fugacity residual
+    of Eq. error small."""
+    from paper_1909_12390_gb300 import lbm
+    t = {r[0]: th.Component(r[0], r[2], r[1], r[3], r[4]) for r in read_table("table1_components.txt")}
+    lb, ts, ps = th.lattice_components([t["C3"], t["nC5"]])
+    T, P, z1 = 666.06 * ts, 200.0 * ps, 0.4
+    fr = th.flash(lb, [[0, 0], [0, 0]], T, P, [z1, 1 - z1])
+    rl, rv, _, _ = th.phase_partial_densities(lb, T, P, 1.0, fr)
+    g_, _ = th.gamma_coefficients(rl, rv, fr.K)
+    L, D, theta = 400, 8.0, lb[0].M / lb[1].M
+    L0 = (rl[0] * z1 + theta * rl[1] * z1 - rl[0]) * L / (
+        2 * (rv[0] - rl[0] - rv[0] * z1 - theta * rv[1] * z1 + rl[0] * z1 + theta * rl[1] * z1))
+    x = np.arange(L, dtype=float)
+    rho = np.empty((2, 2, L))
+    for i in range(2):
+        a = 0.5 * (rl[i] + rv[i]) + 0.5 * (rl[i] - rv[i]) * np.tanh(2 * (x - L0) / D)
+        b = 0.5 * (rl[i] + rv[i]) - 0.5 * (rl[i] - rv[i]) * np.tanh(2 * (x - L + L0) / D)
+        rho[i] = np.where(x <= L / 2, a, b)[None, :]
+    gpu = lbm.Lattice((400, 2), [(k.Tc, k.pc, k.omega, k.M) for k in lb], T=T, tau=0.8, gamma=g_, beta=1.945, G=-1.0)
+    gpu.init(rho)
+    gpu.step(14000)
+    d = gpu.diagnostics(erode=8)
+    gpu.close()
+    assert abs(d["x"][0] / fr.x[0] - 1) < 0.040 and abs(d["y"][0] / fr.y[0] - 1) < 0.040
+    assert abs(sum(d["rho_l"]) / sum(rl) - 1) < 0.021 and abs(sum(d["rho_v"]) / sum(rv) - 1) < 0.021
+    assert d["residual"] < 1e-2
