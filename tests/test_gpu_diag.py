@@ -94,3 +94,41 @@ def test_flat_interface_diagnostics_against_the_flash():
     assert abs(d["x"][0] / fr.x[0] - 1) < 0.040 and abs(d["y"][0] / fr.y[0] - 1) < 0.040
     assert abs(sum(d["rho_l"]) / sum(rl) - 1) < 0.021 and abs(sum(d["rho_v"]) / sum(rv) - 1) < 0.021
     assert d["residual"] < 1e-2
+
+
+@pytest.mark.parametrize("row", read_table("laplace_sigma.txt"))
+def test_laplace_law_surface_tension(row):
+    """Section 4.3: droplets of R0 = nx / 5 in nx x nx periodic domains (nx = 100 .. 250), FP64,
+    40000 steps: dp = p_l - p_v from lbm_diagnostics is linear in 1 / R (R from the liquid
+    area inside the (rho_l + rho_v) / 2 contour) and the slope, the surface tension, is
+    within 5 % of the value the paper prints (its domains run to 800 x 800)."""
+    from paper_1909_12390_gb300 import lbm
+    p_psia, sigma_paper = row
+    t = {r[0]: th.Component(r[0], r[2], r[1], r[3], r[4]) for r in read_table("table1_components.txt")}
+    lb, ts, ps = th.lattice_components([t["C3"], t["nC5"]])
+    T, P = 666.06 * ts, p_psia * ps
+    fr = th.flash(lb, [[0, 0], [0, 0]], T, P, [0.4, 0.6])
+    rl, rv, _, _ = th.phase_partial_densities(lb, T, P, 1.0, fr)
+    g, _ = th.gamma_coefficients(rl, rv, fr.K)
+    R, dp = [], []
+    for nx in (100, 150, 200, 250):
+        R0 = nx / 5
+        yy, xx = np.mgrid[0:nx, 0:nx]
+        r = np.sqrt((xx - nx / 2 + 0.5) ** 2 + (yy - nx / 2 + 0.5) ** 2)
+        # Eq. initialdensity_droplet with the liquid inside (-tanh; the printed +tanh makes a bubble)
+        rho = np.stack([0.5 * (rl[i] + rv[i]) - 0.5 * (rl[i] - rv[i]) * np.tanh(2 * (r - R0) / 4.0) for i in range(2)])
+        gpu = lbm.Lattice((nx, nx), [(k.Tc, k.pc, k.omega, k.M) for k in lb], T=T, tau=0.8, gamma=g, beta=1.915,
+                          G=-1.0)
+        gpu.init(rho)
+        gpu.step(40000)
+        d = gpu.diagnostics(erode=8)
+        gpu.close()
+        R.append(d["radius"])
+        dp.append(d["dp"])
+    R, dp = np.array(R), np.array(dp)
+    A = np.vstack([1.0 / R, np.ones_like(R)]).T
+    (sigma, c), *_ = np.linalg.lstsq(A, dp, rcond=None)
+    print("Laplace %.0f psia: sigma %.5f (paper %.4f), intercept %.2e" % (p_psia, sigma, sigma_paper, c))
+    assert np.max(np.abs(A @ [sigma, c] - dp)) < 0.02 * np.max(dp)
+    assert abs(c) < 0.05 * np.max(dp)
+    assert abs(sigma / sigma_paper - 1) < 0.05
