@@ -64,3 +64,42 @@ def test_elliptical_droplet_period(row):
     print("ellipse nx %d: period %.0f (theory %d, paper model %d)" % (nx, period, theory, model))
     assert theory < period < model * 1.02
     assert abs(period / theory - 1) <= abs(model / theory - 1)
+
+
+def test_flat_interface_spatial_convergence():
+    """Section 4.2's convergence study: the flat interface (C3/nC5 at 200 psia, beta = 1.945,
+    FP64) on nx x 2 grids, nx = 200 .. 3200, 1.5e5 steps; the bulk phase densities approach
+    those of nx = 3200 with every doubling, roughly first order (the paper's reading of its
+    Fig. convergencerate)."""
+    from paper_1909_12390_gb300 import lbm
+    t = {r[0]: th.Component(r[0], r[2], r[1], r[3], r[4]) for r in read_table("table1_components.txt")}
+    lb, ts, ps = th.lattice_components([t["C3"], t["nC5"]])
+    T, P, z1 = 666.06 * ts, 200.0 * ps, 0.4
+    fr = th.flash(lb, [[0, 0], [0, 0]], T, P, [z1, 1 - z1])
+    rl, rv, _, _ = th.phase_partial_densities(lb, T, P, 1.0, fr)
+    g, _ = th.gamma_coefficients(rl, rv, fr.K)
+    D, theta = 8.0, lb[0].M / lb[1].M
+    dens = {}
+    for L in (200, 400, 800, 1600, 3200):
+        # Eq. initialdensity with L0 from Eq. initialdensity2
+        L0 = (rl[0] * z1 + theta * rl[1] * z1 - rl[0]) * L / (
+            2 * (rv[0] - rl[0] - rv[0] * z1 - theta * rv[1] * z1 + rl[0] * z1 + theta * rl[1] * z1))
+        x = np.arange(L, dtype=float)
+        rho = np.empty((2, 2, L))
+        for i in range(2):
+            a = 0.5 * (rl[i] + rv[i]) + 0.5 * (rl[i] - rv[i]) * np.tanh(2 * (x - L0) / D)
+            b = 0.5 * (rl[i] + rv[i]) - 0.5 * (rl[i] - rv[i]) * np.tanh(2 * (x - L + L0) / D)
+            rho[i] = np.where(x <= L / 2, a, b)[None, :]
+        gpu = lbm.Lattice((L, 2), [(k.Tc, k.pc, k.omega, k.M) for k in lb], T=T, tau=0.8, gamma=g, beta=1.945, G=-1.0)
+        gpu.init(rho)
+        gpu.step(150000)
+        d = gpu.diagnostics(erode=8)
+        gpu.close()
+        dens[L] = (sum(d["rho_l"]), sum(d["rho_v"]))
+    for ph in (0, 1):
+        ref = dens[3200][ph]
+        err = [abs(dens[L][ph] / ref - 1) for L in (200, 400, 800, 1600)]
+        print("flat interface phase %d: errors against nx = 3200: %s" % (ph, ["%.2e" % e for e in err]))
+        assert all(a > b for a, b in zip(err, err[1:])), err
+        order = np.mean(np.log2(np.array(err[:-1]) / np.array(err[1:])))
+        assert 0.5 < order < 2.0, order
