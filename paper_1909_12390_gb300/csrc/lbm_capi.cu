@@ -278,8 +278,7 @@ bool setup_fused3(lbm_ctx* c) {
   bool fits = false;
   for (int tries = 0; tries < 4 && G >= 2; ++tries) {
     smax = (int)((nxy + G - 1) / G);
-    const size_t smem = (size_t)2 * (lbm::kF3Lead + 1) * (c->nc + 3) * smax * c->ops->arith_bytes;
-    if (smem > 160 * 1024) return false;
+    const size_t smem = 0;
     const int cap = c->ops->fused3_max_blocks((int)smem);  // co-resident CTAs
     if (cap >= G / 2) {
       fits = true;

@@ -4,9 +4,9 @@
 // (y, x) index of a z plane and marches z = 0 .. nz-1, with psi computed LEAD planes ahead of the collision
 // (LEAD = LBM_F3_LEAD). Before the march it computes psi of plane nz - 1 and of planes
 // 0 .. LEAD - 1. Iteration k then
-//   1. reads the populations of plane k + LEAD of its range once from DRAM (the psi stage):
-//      the moments of every site (shifted densities and momentum, kept per thread for the
-//      collision) and from them the mixture EOS and psi, written to the psi plane buffer;
+//   1. reads the populations of plane k + LEAD of its range from DRAM (the psi stage): the
+//      densities of every site and from them the mixture EOS and psi, written to the psi
+//      plane buffer;
 //   2. publishes its progress (psi done up to plane k + LEAD) with st.release.gpu and waits
 //      (bounded ld.acquire.gpu polls) until every worker owning a neighbour site has psi of
 //      plane k + 1; with LEAD = 2 the neighbours published that an iteration earlier, so they
@@ -74,7 +74,6 @@ __device__ __forceinline__ void fused3_body(const Params& P, typename Prec::S* _
   using R = typename Prec::R;
   using PsiT = typename Prec::PsiT;
   using L = Lat<Q>;
-  extern __shared__ __align__(16) unsigned char f3_smem[];
   __shared__ int nbr_s[2][kF3MaxNbr];
   __shared__ int n_nbr_s[2];
 
@@ -82,9 +81,7 @@ __device__ __forceinline__ void fused3_body(const Params& P, typename Prec::S* _
   const int tid = threadIdx.x - half * kF3Worker;
   const int w = 2 * blockIdx.x + half;  // worker
   const int bar = 1 + half;
-  const int r0 = A.range[w], S = A.range[w + 1] - r0, SM = A.smax;
-  // [worker][LEAD + 1][NC + 3][smax]: moments of planes k .. k + LEAD
-  R* mom = reinterpret_cast<R*>(f3_smem) + (size_t)half * (kF3Lead + 1) * (NC + 3) * SM;
+  const int r0 = A.range[w], S = A.range[w + 1] - r0;
   int* nbr = nbr_s[half];
   const int nx = P.nx, nz = P.nz, nxy = P.nx * P.ny;
   // progress value: last plane with psi published + 2, at most nz + LEAD + 1 in a launch
@@ -106,26 +103,21 @@ __device__ __forceinline__ void fused3_body(const Params& P, typename Prec::S* _
 
   int err = 0;
   bool ok = true;
-  // psi stage of plane z: moments (kept in buffer buf when keep) and psi (written when put)
-  auto stage = [&](int z, int buf, bool put, bool keep) {
+  // psi stage of plane z (psi written when put; the plane's populations come through L2 for
+  // the collision, which recomputes the site moments: that pass brings all of a site's
+  // populations into L1 with every load in flight before the per-component passes)
+  auto stage = [&](int z, bool put) {
     PsiT* dst = plane(z);
-    R* m = mom + (size_t)buf * (NC + 3) * SM;
     for (int i = tid; i < S; i += kF3Worker) {
       const int xy = r0 + i;
       Site st;
       st.set_xyz(P, xy % nx, xy / nx, z);
-      R dl[NC], j[3];
-      site_moments<Q, NC, Prec, PAR>(P, f, st, dl, j);
+      R dl[NC];
+      site_densities<Q, NC, Prec, PAR>(P, f, st, dl);
       if (put) {
         PsiT v;
         err |= site_psi_dl<NC, Prec>(P, dl, v);
         dst[xy] = v;
-      }
-      if (keep) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) m[c * SM + i] = dl[c];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) m[(NC + d) * SM + i] = j[d];
       }
     }
   };
@@ -149,9 +141,8 @@ __device__ __forceinline__ void fused3_body(const Params& P, typename Prec::S* _
     }
     ok = f3_bar_and(bar, mine && ok);
   };
-  auto collide = [&](int z, int buf) {
+  auto collide = [&](int z) {
     const PsiT* pl[3] = {plane(z - 1), plane(z), plane(z + 1)};
-    const R* m = mom + (size_t)buf * (NC + 3) * SM;
 #pragma unroll 1
     for (int i = tid; i < S; i += kF3Worker) {
       const int xy = r0 + i;
@@ -167,28 +158,23 @@ __device__ __forceinline__ void fused3_body(const Params& P, typename Prec::S* _
         const int row = ey < 0 ? ym : (ey > 0 ? yp : y0);
         pn[A_] = (R)__ldcg(pl[ez + 1] + row + col);
       });
-      R dl[NC], j[3];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) dl[c] = m[c * SM + i];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) j[d] = m[(NC + d) * SM + i];
-      site_collide_m<Q, NC, Prec, MRT, PAR>(P, f, st, pn, dl, j);
+      site_collide<Q, NC, Prec, MRT, PAR>(P, f, st, pn);
     }
   };
 
   // worker 1 starts once worker 0 has done its first psi stage (barrier 3 spans the CTA)
   if (half == 1) asm volatile("bar.sync 3, %0;" ::"r"(kF3Threads) : "memory");
-  stage(nz - 1, 0, true, false);
+  stage(nz - 1, true);
   if (half == 0) asm volatile("bar.arrive 3, %0;" ::"r"(kF3Threads) : "memory");
-  for (int p = 0; p < kF3Lead && p < nz; ++p) stage(p, p, p < nz - 1, true);
+  for (int p = 0; p < kF3Lead && p < nz; ++p) stage(p, p < nz - 1);
   publish(kF3Lead + 1);
   for (int k = 0; k < nz; ++k) {
     const int q = k + kF3Lead;
-    if (q < nz) stage(q, q % (kF3Lead + 1), q < nz - 1, true);
+    if (q < nz) stage(q, q < nz - 1);
     publish(q + 2);
     wait(k + 3);
     if (!ok) break;
-    collide(k, k % (kF3Lead + 1));
+    collide(k);
   }
   if (!ok) err |= ST_TIMEOUT;
   // finish: the last CTA of the launch folds the pending status and advances the step

@@ -1003,7 +1003,7 @@ struct Launch {
       Params Pc = P;
       FusedArgs Ac = A;
       void* args[] = {(void*)&Pc, (void*)&fp, (void*)&st, (void*)&t_dev, (void*)&Ac};
-      const size_t smem = (size_t)2 * (kF3Lead + 1) * (NC + 3) * A.smax * sizeof(R);
+      const size_t smem = 0;
       return cudaLaunchCooperativeKernel((const void*)k_fused3<NC, Prec, MRT>, dim3((unsigned)(A.G / 2)),
                                          dim3(kF3Threads), args, smem, s);
     }
