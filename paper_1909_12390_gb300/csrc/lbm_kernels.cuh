@@ -34,10 +34,10 @@ constexpr int kBlock = 256;
 // Collide pass: threads per block and resident blocks per SM, which set its register budget
 // (an SM sub-partition's 16 K registers: 4 warps of 128 or 3 of 168 registers).
 #ifndef LBM_COLLIDE_THREADS
-#define LBM_COLLIDE_THREADS 256
+#define LBM_COLLIDE_THREADS 128
 #endif
 #ifndef LBM_COLLIDE_BLOCKS
-#define LBM_COLLIDE_BLOCKS 2
+#define LBM_COLLIDE_BLOCKS 4
 #endif
 constexpr int kCollideThreads = LBM_COLLIDE_THREADS;
 constexpr int kCollideBlocks = LBM_COLLIDE_BLOCKS;
@@ -129,10 +129,6 @@ __device__ __forceinline__ int site_psi(const Params& P, const typename Prec::S*
 // not merged with what was computed from it before.
 __device__ __forceinline__ void opaque(float& x) { asm volatile("" : "+f"(x)); }
 __device__ __forceinline__ void opaque(double& x) { asm volatile("" : "+d"(x)); }
-__device__ __forceinline__ void opaque(Site& t) {
-  asm volatile("" : "+r"(t.idx), "+r"(t.x), "+r"(t.y), "+r"(t.z));
-  asm volatile("" : "+r"(t.xm), "+r"(t.xp), "+r"(t.ym), "+r"(t.yp), "+r"(t.zm), "+r"(t.zp));
-}
 
 // Population load that the optimiser keeps where it is written: a plain load of the same
 // address (the moments pass read every population already) would be merged with the earlier
@@ -312,16 +308,13 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
     // q = g + chi Fb / 2 in pair form (q_a + q_b = g_a + g_b + chi Fe, q_a - q_b =
     // g_a - g_b + chi Fo; even rows through per-class sums, odd rows directly); the second
     // pass re-reads the populations (L1), forms d and the MRT correction and stores. Keeping
-    // nothing per pair between the passes holds the register count without spills.
+    // nothing per pair between the passes keeps the register count down.
     // Per-pair values are the same for every component and both passes; the compiler would
     // compute them once and hold 2 (Q - 1) or more registers through the whole loop. Passing
     // u, F and u.F through an empty asm makes them opaque per pass, so they are recomputed
     // (a few FMAs per pair) instead.
     R uo[3], Fo_[3], uFo = uF, P0o = P0;
-    Site so = s;  // the site's addresses, likewise recomputed per pass
     auto refresh = [&]() {
-      so = s;
-      opaque(so);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         uo[d] = u[d];
@@ -359,8 +352,8 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
       For<0, NP>::run([&]<int K>() {
         constexpr int a = L::pfirst(K), b = L::opp(a);
         R ga, gb, Fe, Fo;
-        pair_g(std::integral_constant<int, K>{}, (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, so)),
-               (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, so)), ga, gb, Fe, Fo);
+        pair_g(std::integral_constant<int, K>{}, (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, s)),
+               (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, s)), ga, gb, Fe, Fo);
         cs[pclass<Q>(K)] += (ga + gb) + chi * Fe;
         const R qm = (ga - gb) + chi * Fo;
         For<0, L::NK>::run([&]<int I>() {
@@ -397,8 +390,8 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
     refresh();
     For<0, NP>::run([&]<int K>() {
       constexpr int a = L::pfirst(K), b = L::opp(a);
-      const R va = (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, so));
-      const R vb = (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, so));
+      const R va = (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, s));
+      const R vb = (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, s));
       R ga, gb, Fe, Fo;
       pair_g(std::integral_constant<int, K>{}, va, vb, ga, gb, Fe, Fo);
       R da = gkchi * (Fe + Fo) - om * ga;
@@ -421,8 +414,8 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
       const R oa = va + da;
       const R ob = vb + db;
       if constexpr (sizeof(R) == 4) rest -= oa + ob;
-      store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<a, PAR>(P, so), oa);
-      store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<b, PAR>(P, so), ob);
+      store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<a, PAR>(P, s), oa);
+      store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<b, PAR>(P, s), ob);
     });
     // The weights rounded to FP32 sum to 1 + 7.5e-9 (D2Q9) or 1 + 1.5e-8 (D3Q19), which makes
     // every step scale the stored deviation rho_c - rho_ref_c by 1 + omega * that excess: a
