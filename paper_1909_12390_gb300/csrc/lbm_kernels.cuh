@@ -132,16 +132,18 @@ __device__ __forceinline__ void opaque(double& x) { asm volatile("" : "+d"(x)); 
 
 // Population load that the optimiser keeps where it is written: a plain load of the same
 // address (the moments pass read every population already) would be merged with the earlier
-// one and keep Q * NC values in registers through the collision. Generic addressing, so the
+// one and keep Q * NC values in registers through the collision. The "memory" clobber keeps
+// it ordered with the stores: in the in-place update of a pair (a, b) the new value for a
+// goes to b's slot, and it must not be stored before b's value has been read. Generic addressing, so the
 // same code serves populations in global and in shared memory.
 __device__ __forceinline__ float ld_pop(const float* p) {
   float v;
-  asm volatile("ld.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  asm volatile("ld.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ double ld_pop(const double* p) {
   double v;
-  asm volatile("ld.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  asm volatile("ld.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
   return v;
 }
 
