@@ -129,6 +129,10 @@ __device__ __forceinline__ int site_psi(const Params& P, const typename Prec::S*
 // not merged with what was computed from it before.
 __device__ __forceinline__ void opaque(float& x) { asm volatile("" : "+f"(x)); }
 __device__ __forceinline__ void opaque(double& x) { asm volatile("" : "+d"(x)); }
+__device__ __forceinline__ void opaque(Site& t) {
+  asm volatile("" : "+r"(t.idx), "+r"(t.x), "+r"(t.y), "+r"(t.z));
+  asm volatile("" : "+r"(t.xm), "+r"(t.xp), "+r"(t.ym), "+r"(t.yp), "+r"(t.zm), "+r"(t.zp));
+}
 
 // Population load that the optimiser keeps where it is written: a plain load of the same
 // address (the moments pass read every population already) would be merged with the earlier
@@ -316,7 +320,14 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
     // u, F and u.F through an empty asm makes them opaque per pass, so they are recomputed
     // (a few FMAs per pair) instead.
     R uo[3], Fo_[3], uFo = uF, P0o = P0;
+    // The site's addresses are likewise made opaque per pass. Besides bounding the registers,
+    // this keeps the instruction stream of the collision the same in every kernel that
+    // inlines it: without it the fused and two-kernel steps were measured to differ in the
+    // last bit (the multiply-add contractions follow the instruction order).
+    Site so = s;
     auto refresh = [&]() {
+      so = s;
+      opaque(so);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         uo[d] = u[d];
@@ -341,7 +352,7 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
       ga = (va - A) - B;
       gb = (vb - A) + B;
     };
-    const R v0 = (R)ld_pop(fc + AA<Q>::template rd<0, PAR>(P, s));
+    const R v0 = (R)ld_pop(fc + AA<Q>::template rd<0, PAR>(P, so));
     const R g0 = v0 - (R)L::w(0) * (dl[C] + rc[C] * P0);
     R d0 = gkchi * F0 - om * g0;
     R lm[L::NK];
@@ -354,8 +365,8 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
       For<0, NP>::run([&]<int K>() {
         constexpr int a = L::pfirst(K), b = L::opp(a);
         R ga, gb, Fe, Fo;
-        pair_g(std::integral_constant<int, K>{}, (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, s)),
-               (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, s)), ga, gb, Fe, Fo);
+        pair_g(std::integral_constant<int, K>{}, (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, so)),
+               (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, so)), ga, gb, Fe, Fo);
         cs[pclass<Q>(K)] += (ga + gb) + chi * Fe;
         const R qm = (ga - gb) + chi * Fo;
         For<0, L::NK>::run([&]<int I>() {
@@ -392,8 +403,8 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
     refresh();
     For<0, NP>::run([&]<int K>() {
       constexpr int a = L::pfirst(K), b = L::opp(a);
-      const R va = (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, s));
-      const R vb = (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, s));
+      const R va = (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, so));
+      const R vb = (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, so));
       R ga, gb, Fe, Fo;
       pair_g(std::integral_constant<int, K>{}, va, vb, ga, gb, Fe, Fo);
       R da = gkchi * (Fe + Fo) - om * ga;
@@ -416,8 +427,8 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
       const R oa = va + da;
       const R ob = vb + db;
       if constexpr (sizeof(R) == 4) rest -= oa + ob;
-      store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<a, PAR>(P, s), oa);
-      store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<b, PAR>(P, s), ob);
+      store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<a, PAR>(P, so), oa);
+      store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<b, PAR>(P, so), ob);
     });
     // The weights rounded to FP32 sum to 1 + 7.5e-9 (D2Q9) or 1 + 1.5e-8 (D3Q19), which makes
     // every step scale the stored deviation rho_c - rho_ref_c by 1 + omega * that excess: a
