@@ -158,15 +158,16 @@ def _oracle_sample(c, n):
                        gamma=c["gamma"], kij=c["kij"], beta=c["beta"], G=c["G"], collision=1,
                        s=c["mrt_s"])
     rho = lbm_inputs.ball_fields((n, n, n), c["rho_l"], c["rho_v"], 48.0 * n / 256, c["init"]["width"])
-    return case, oracle.equilibrium(case, rho)
+    return case, oracle.equilibrium(case, rho), rho
 
 
 def cpu_baseline(c, target_s=12.0, n=64):
     """The oracle as it stands on the host cores: D3Q19 MRT steps of a periodic n^3 sample of
     the workload (same constants, droplet radius scaled with the box), timed until about
-    target_s of CPU work."""
+    target_s of CPU work. Returns the baseline entry and the sample's end state (case, initial
+    densities, steps taken, final populations)."""
     import oracle
-    case, f = _oracle_sample(c, n)
+    case, f, rho0 = _oracle_sample(c, n)
     f = oracle.step(case, f, 1)  # warm-up (thread pool, pages)
     steps, t0 = 0, time.perf_counter()
     while True:
@@ -176,9 +177,32 @@ def cpu_baseline(c, target_s=12.0, n=64):
         if el > target_s:
             break
     val = n ** 3 * case.nc * steps / el / 1e6
-    return {"value": val, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": "%d steps of a periodic %d^3 D3Q19 MRT FP64 sample of the workload (3 components)"
-                      % (steps, n)}
+    return ({"value": val, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+             "sample": "%d steps of a periodic %d^3 D3Q19 MRT FP64 sample of the workload (3 components)"
+                       % (steps, n)}, (case, rho0, steps + 1, f))
+
+
+def accuracy(c, sample):
+    """Error of the FP32-shifted and FP64 paths against the oracle on the baseline's sample:
+    the same initial densities and step count on the GPU, max over sites and components of
+    |rho_s - rho_s,oracle| / sum_s rho_s,oracle."""
+    import oracle
+    from paper_1909_12390_gb300 import lbm
+    case, rho0, steps, f = sample
+    ro = oracle.fields(case, f).rho
+    n = rho0.shape[-1]
+    cs = dict(c, shape=[n, n, n])
+    out = {"measure": "max over sites and components of |rho_s - rho_s,oracle| / sum_s rho_s,oracle",
+           "sample": "periodic %d^3 sample of the workload after %d steps (the cpu_baseline run)" % (n, steps)}
+    for name, prec in (("fp32s", lbm.FP32_SHIFTED), ("fp64", lbm.FP64)):
+        g = lattice_for(cs, prec)
+        g.init(rho0)
+        g.step(steps)
+        rg = g.fields(u=False, p=False, psi=False)["rho"]
+        g.close()
+        out[name] = float(np.max(np.abs(rg - ro) / ro.sum(0)))
+    out["tolerance"] = {"fp32s": 2e-4, "fp64": 1e-10}
+    return out
 
 
 def run_reference(args, rank):
@@ -189,7 +213,7 @@ def run_reference(args, rank):
     import oracle
     c = load_case()
     n = 32
-    case, f = _oracle_sample(c, n)
+    case, f, _ = _oracle_sample(c, n)
     f = oracle.step(case, f, args.warmup)
     t0 = time.perf_counter()
     f = oracle.step(case, f, args.steps)
@@ -443,7 +467,8 @@ def main():
     if variants:
         out["variants"] = variants
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(c)
+        out["cpu_baseline"], sample = cpu_baseline(c)
+        out["err_vs_oracle"] = accuracy(c, sample)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

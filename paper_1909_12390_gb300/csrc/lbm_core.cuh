@@ -5,6 +5,7 @@
 // direction index so that fully unrolled loops fold every lattice constant.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 
 namespace lbm {
@@ -187,6 +188,10 @@ struct Params {
   double k1, k2;      // pair form of the force: -G / 36, -(1 - beta) G / 72 (weights counted in 1/36)
   float omega_f, gk_f, c1_f, c2_f, cpsi_f, k1_f, k2_f;
   float lam_f[10], rho_ref_f[4], gamma_f[4];
+  // the FP32-input EOS works with p / RT: sa_i / sqrt(RT), Qa_ii / RT and 2 Qa_ij / RT (i < j);
+  // psi^2 = cpsi RT (p / RT - rho / (3 RT))
+  double sa_rt[4], Qa_rt[16];
+  float cpsi_rt_f, c3rt_f;
 };
 
 // Fills the derived constants of P (call after any change of omega, lam, rho_ref, gamma,
@@ -209,6 +214,12 @@ inline void finalize_params(Params& P) {
     P.rho_ref_f[i] = (float)P.rho_ref[i];
     P.gamma_f[i] = (float)P.gamma[i];
   }
+  for (int i = 0; i < 4; ++i) {
+    P.sa_rt[i] = P.RT > 0 ? P.sa[i] / std::sqrt(P.RT) : 0.0;
+    for (int j = 0; j < 4; ++j) P.Qa_rt[i * 4 + j] = P.RT > 0 ? (i == j ? 1.0 : 2.0) * P.Qa[i * 4 + j] / P.RT : 0.0;
+  }
+  P.cpsi_rt_f = (float)(P.cpsi * P.RT);
+  P.c3rt_f = P.RT > 0 ? (float)(1.0 / (3.0 * P.RT)) : 0.0f;
 }
 
 // Per-site constants in the arithmetic precision R of a kernel.
@@ -356,42 +367,115 @@ __device__ __forceinline__ EosOut<NC> eos_pr(const Params& P, const double (&rho
   return o;
 }
 
-// The same pressure from FP32 cell-volume densities (FP32-shifted storage): the molar
-// densities n_i = rho_i / M_i are formed in FP32 (their inputs carry FP32 precision), every
-// sum of the EOS and the numerator with its cancellation run in FP64. With all zeta_ij = 0
-// the mixing rule collapses to A2 = (sum_i n_i sqrt(a_i alpha_i))^2.
-template <int NC>
-__device__ __forceinline__ EosOut<NC> eos_pr_f32in(const Params& P, const float (&rho)[NC]) {
-  double n[NC];
-  double nt = 0.0, B = 0.0;
+// Conversions between binary32 and binary64 in integer arithmetic (IEEE 754 formats). On
+// GB300 a conversion instruction occupies the FP64 pipe like an FP64 multiply-add, and the
+// pseudo-potential pass is bound by that pipe; the integer forms below run on the integer
+// pipes. Each covers the common case exactly and reports whether it applies; callers fall back
+// to the conversion instruction, warp by warp, for the rest.
+//
+// Widening of a positive normal binary32 value (exact): the biased exponent gains
+// 1023 - 127 = 896 and the 23 fraction bits become the top 23 of the 52.
+__device__ __forceinline__ bool widen_int_ok(float x) {
+  return __float_as_uint(x) - 0x00800000u < 0x7f000000u;  // sign 0, biased exponent 1 .. 254
+}
+__device__ __forceinline__ double widen_int(float x) {
+  const unsigned u = __float_as_uint(x);
+  return __hiloint2double((int)((u >> 3) + 0x38000000u), (int)(u << 29));
+}
+// Narrowing with round to nearest, ties to even, for |x| whose binary32 result is a normal
+// number or overflows to infinity: biased binary64 exponent 897 .. 1150. The 23 fraction bits
+// are the top of the 52, the 29 bits below them decide the rounding, and a carry out of the
+// fraction increments the exponent (up to infinity), as rounding requires.
+__device__ __forceinline__ bool narrow_int_ok(double x) {
+  return ((unsigned)__double2hiint(x) & 0x7fffffffu) - 0x38100000u < 0x0fe00000u;
+}
+__device__ __forceinline__ float narrow_int(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  unsigned f = (((hi & 0x7fffffffu) - 0x38000000u) << 3) | (lo >> 29);
+  const unsigned r = lo & 0x1fffffffu;
+  f += (unsigned)(r > 0x10000000u) | ((unsigned)(r == 0x10000000u) & (f & 1u));
+  return __uint_as_float(f | (hi & 0x80000000u));
+}
+// Element-wise conversions of small arrays; a warp takes the conversion instruction only when
+// one of its lanes has a value outside the integer forms' range.
+template <int N>
+__device__ __forceinline__ void widen_all(const float (&x)[N], double (&y)[N]) {
+  bool ok = true;
 #pragma unroll
-  for (int i = 0; i < NC; ++i) {
-    n[i] = (double)(rho[i] * P.invMf[i]);
+  for (int i = 0; i < N; ++i) {
+    y[i] = widen_int(x[i]);
+    ok = ok && widen_int_ok(x[i]);
+  }
+  if (__any_sync(__activemask(), !ok)) {
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (!widen_int_ok(x[i])) y[i] = (double)x[i];
+  }
+}
+template <int N>
+__device__ __forceinline__ void narrow_all(const double (&x)[N], float (&y)[N]) {
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    y[i] = narrow_int(x[i]);
+    ok = ok && narrow_int_ok(x[i]);
+  }
+  if (__any_sync(__activemask(), !ok)) {
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (!narrow_int_ok(x[i])) y[i] = (float)x[i];
+  }
+}
+
+// The same pressure from FP32 cell-volume densities (FP32-shifted storage), returned as
+// pD / Dd = p / RT. The molar densities n_i = rho_i / M_i are formed in FP32 (their inputs
+// carry FP32 precision) and widened exactly; every sum of the EOS and the numerator with its
+// cancellation run in FP64:
+//   B = sum b_i n_i,  A2' = sum_ij n_i n_j Qa_ij / RT  (= (sum_i n_i sa_i / sqrt(RT))^2 when
+//   all zeta_ij = 0),  d1 = 1 - B,  d2 = 1 + 2B - B^2 = 2 - d1^2,
+//   pD = n d2 - A2' d1,  Dd = d1 d2.
+// Dividing through by RT saves the multiplication n RT; d2 from d1 saves the subtraction 2 - B.
+// ok is B < 1 (d1 > 0), tested on the sign and exponent bits of d1.
+struct EosOutF {
+  double pD, Dd;
+  bool ok;
+};
+
+template <int NC>
+__device__ __forceinline__ EosOutF eos_pr_f32in(const Params& P, const float (&rho)[NC]) {
+  float nf[NC];
+#pragma unroll
+  for (int i = 0; i < NC; ++i) nf[i] = rho[i] * P.invMf[i];
+  double n[NC];
+  widen_all<NC>(nf, n);
+  double nt = n[0], B = P.b[0] * n[0];
+#pragma unroll
+  for (int i = 1; i < NC; ++i) {
     nt += n[i];
     B = fma(P.b[i], n[i], B);
   }
   double A2;
   if (P.kij_zero) {
-    double S = 0.0;
+    double S = P.sa_rt[0] * n[0];
 #pragma unroll
-    for (int i = 0; i < NC; ++i) S = fma(P.sa[i], n[i], S);
+    for (int i = 1; i < NC; ++i) S = fma(P.sa_rt[i], n[i], S);
     A2 = S * S;
   } else {
     A2 = 0.0;
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-      double v = P.Qa[i * 4 + i] * n[i];
+      double v = P.Qa_rt[i * 4 + i] * n[i];
 #pragma unroll
-      for (int j = i + 1; j < NC; ++j) v = fma(2.0 * P.Qa[i * 4 + j], n[j], v);
+      for (int j = i + 1; j < NC; ++j) v = fma(P.Qa_rt[i * 4 + j], n[j], v);
       A2 = fma(n[i], v, A2);
     }
   }
-  double d1 = 1.0 - B;
-  double d2 = fma(B, 2.0 - B, 1.0);
-  EosOut<NC> o;
+  const double d1 = 1.0 - B;
+  const double d2 = fma(-d1, d1, 2.0);
+  EosOutF o;
   o.Dd = d1 * d2;
-  o.pD = fma(nt * P.RT, d2, -A2 * d1);
-  o.B = B;
+  o.pD = fma(nt, d2, -A2 * d1);
+  o.ok = __double2hiint(d1) > 0;
   return o;
 }
 

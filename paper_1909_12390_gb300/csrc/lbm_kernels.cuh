@@ -70,7 +70,8 @@ __device__ __forceinline__ int site_psi_dl(const Params& P, const typename Prec:
                                            typename Prec::PsiT& psi_out) {
   using R = typename Prec::R;
   R rho_t = 0;
-  double pD, Dd, B;
+  R psi2;
+  bool dom;  // B < 1
   if constexpr (sizeof(R) == 8) {
     double rho[NC];
 #pragma unroll
@@ -79,7 +80,8 @@ __device__ __forceinline__ int site_psi_dl(const Params& P, const typename Prec:
       rho_t += rho[i];
     }
     EosOut<NC> e = eos_pr<NC>(P, rho);
-    pD = e.pD; Dd = e.Dd; B = e.B;
+    psi2 = P.cpsi * (e.pD / e.Dd - rho_t * (1.0 / 3.0));
+    dom = e.B < 1.0;
   } else {
     float rc[NC];
 #pragma unroll
@@ -87,19 +89,18 @@ __device__ __forceinline__ int site_psi_dl(const Params& P, const typename Prec:
       rc[i] = P.rho_ref_f[i] + d[i];
       rho_t += rc[i];
     }
-    EosOut<NC> e = eos_pr_f32in<NC>(P, rc);
-    pD = e.pD; Dd = e.Dd; B = e.B;
-  }
-  R psi2;
-  if constexpr (sizeof(R) == 8) {
-    psi2 = P.cpsi * (pD / Dd - rho_t * (1.0 / 3.0));
-  } else {
-    // the quotient and everything after it are well conditioned: FP32, like the stored psi
-    psi2 = P.cpsi_f * ((float)pD / (float)Dd - rho_t * (1.0f / 3.0f));
+    EosOutF e = eos_pr_f32in<NC>(P, rc);
+    // the quotient and everything after it are well conditioned: FP32, like the stored psi;
+    // psi^2 = cpsi RT (p / RT - rho / (3 RT))
+    const double pq[2] = {e.pD, e.Dd};
+    float q[2];
+    narrow_all<2>(pq, q);
+    psi2 = P.cpsi_rt_f * (q[0] / q[1] - rho_t * P.c3rt_f);
+    dom = e.ok;
   }
   psi_out = 0;
   if (!isfinite(psi2) || !isfinite(rho_t)) return ST_NONFINITE;
-  if (!(B < 1.0) || psi2 < (R)0) return ST_PSI_DOMAIN;
+  if (!dom || psi2 < (R)0) return ST_PSI_DOMAIN;
   psi_out = (typename Prec::PsiT)sqrt(psi2);
   return 0;
 }
