@@ -252,13 +252,17 @@ void free_fused(lbm_ctx* c) {
   c->fused = false;
 }
 
-// Blocks (CTAs) of the active fused kernel.
+// Workers (plane ranges) of the plane-range kernel, or blocks of the tile-column kernel.
 int fused_blocks(const lbm_ctx* c) {
   return c->fargs.mode == 3 ? c->fargs.G : c->fargs.ntx * c->fargs.nty * c->fargs.nchunk;
 }
+// Progress counters of the active fused kernel.
+int fused_flags(const lbm_ctx* c) {
+  return c->fargs.mode == 3 ? c->fargs.G * c->ops->fused3_flags : fused_blocks(c);
+}
 
-// The plane-range fused step (k_fused3, D3Q19): one CTA per SM of two workers, G workers in
-// all, worker w owning sites [w nxy / G, (w + 1) nxy / G) of every z plane; the neighbour
+// The plane-range fused step (k_fused3, D3Q19): one CTA per SM of ops->fused3_wpc workers,
+// G workers in all, worker w owning sites [w nxy / G, (w + 1) nxy / G) of every z plane; the neighbour
 // workers of each worker (owners of the 8 in-plane neighbours of its sites) are listed for its
 // waits. Returns false when the grid is too small or a worker would have more than kF3MaxNbr
 // neighbours.
@@ -273,19 +277,20 @@ bool setup_fused3(lbm_ctx* c) {
     cudaGetLastError();
     return false;
   }
-  int G = 2 * (int)std::min<long long>(sms, nxy / 64);  // workers, two per CTA
+  const int WPC = c->ops->fused3_wpc;
+  int G = WPC * (int)std::min<long long>(sms, nxy / 64);  // workers
   int smax = 0;
   bool fits = false;
   for (int tries = 0; tries < 4 && G >= 2; ++tries) {
     smax = (int)((nxy + G - 1) / G);
     const size_t smem = 0;
     const int cap = c->ops->fused3_max_blocks((int)smem);  // co-resident CTAs
-    if (cap >= G / 2) {
+    if (cap >= G / WPC) {
       fits = true;
       break;
     }
     if (cap <= 0) return false;
-    G = 2 * cap;
+    G = WPC * cap;
   }
   if (!fits) return false;
   std::vector<int> range(G + 1), owner(nxy), nbr((size_t)G * lbm::kF3MaxNbr, -1);
@@ -315,14 +320,15 @@ bool setup_fused3(lbm_ctx* c) {
   a.silent_block = -1;
   int* d_range = nullptr;
   int* d_nbr = nullptr;
-  bool ok = cudaMalloc(&a.flags, (size_t)G * sizeof(unsigned long long)) == cudaSuccess &&
+  const size_t nflags = (size_t)G * c->ops->fused3_flags;
+  bool ok = cudaMalloc(&a.flags, nflags * sizeof(unsigned long long)) == cudaSuccess &&
             cudaMalloc(&a.done, sizeof(unsigned int)) == cudaSuccess && cudaMalloc(&a.pending, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&d_range, (G + 1) * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&d_nbr, nbr.size() * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&a.psi_ring, (size_t)(lbm::kF3Ring + 2) * nxy * c->ops->psi_bytes) == cudaSuccess;
   a.range = d_range;
   a.nbr = d_nbr;
-  ok = ok && cudaMemset(a.flags, 0, (size_t)G * sizeof(unsigned long long)) == cudaSuccess &&
+  ok = ok && cudaMemset(a.flags, 0, nflags * sizeof(unsigned long long)) == cudaSuccess &&
        cudaMemset(a.done, 0, sizeof(unsigned int)) == cudaSuccess && cudaMemset(a.pending, 0, sizeof(int)) == cudaSuccess &&
        cudaMemcpy(d_range, range.data(), (G + 1) * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -391,7 +397,7 @@ bool setup_auto(lbm_ctx* c) {
 // Progress counters must not exceed t * L when the step counter is reset or rewound.
 cudaError_t reset_fused_flags(lbm_ctx* c) {
   if (!c->fused) return cudaSuccess;
-  return cudaMemsetAsync(c->fargs.flags, 0, (size_t)fused_blocks(c) * sizeof(unsigned long long), c->stream);
+  return cudaMemsetAsync(c->fargs.flags, 0, (size_t)fused_flags(c) * sizeof(unsigned long long), c->stream);
 }
 
 // Captures kGraphSteps steps starting at an even step; on any capture failure the context

@@ -313,6 +313,12 @@ __device__ __forceinline__ T* comp_base(T* f, const Params& P, int c) {
   return f + (size_t)c * Q * P.N;
 }
 
+// Multiply-add with one rounding. The library is compiled with -fmad=false, so the compiler
+// forms no multiply-add of its own: every one is written out here, and the per-site code
+// rounds identically in every kernel that inlines it (the paths are compared bit for bit).
+__device__ __forceinline__ float fmx(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmx(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Compile-time loop.
 template <int I, int N>
 struct For {

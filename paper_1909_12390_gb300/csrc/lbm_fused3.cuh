@@ -32,6 +32,9 @@
 
 namespace lbm {
 
+constexpr int kF3WorkersPerCta = 2;  // workers (plane ranges) per CTA
+constexpr int kF3FlagSets = 1;       // progress counters per worker
+
 #ifndef LBM_F3_LEAD
 #define LBM_F3_LEAD 1
 #endif
@@ -195,6 +198,8 @@ __device__ __forceinline__ void fused3_body(const Params& P, typename Prec::S* _
     }
   }
 }
+
+
 
 // One CTA per SM; the launch bound sets the register budget (see kF3Bound).
 template <int NC, class Prec, int MRT>

@@ -86,7 +86,7 @@ __device__ __forceinline__ int site_psi_dl(const Params& P, const typename Prec:
       rho_t += rho[i];
     }
     EosOut<NC> e = eos_pr<NC>(P, rho);
-    psi2 = P.cpsi * (e.pD / e.Dd - rho_t * (1.0 / 3.0));
+    psi2 = P.cpsi * fmx(-rho_t, 1.0 / 3.0, e.pD / e.Dd);
     dom = e.B < 1.0;
   } else {
     float rc[NC];
@@ -101,7 +101,7 @@ __device__ __forceinline__ int site_psi_dl(const Params& P, const typename Prec:
     const double pq[2] = {e.pD, e.Dd};
     float q[2];
     narrow_all<2>(pq, q);
-    psi2 = P.cpsi_rt_f * (q[0] / q[1] - rho_t * P.c3rt_f);
+    psi2 = P.cpsi_rt_f * fmx(-rho_t, P.c3rt_f, q[0] / q[1]);
     dom = e.ok;
   }
   psi_out = 0;
@@ -223,8 +223,9 @@ __device__ __forceinline__ void site_moments(const Params& P, const typename Pre
 // and the site's moments: total force, split, Guo-forced BGK or MRT collision, in-place AA
 // write. Everything is arranged over the pairs of opposite directions (a, b = opp(a)):
 //   * the equilibrium is w_a (dl_c + rho_c P_a) with P_a = Pe +- Po (even / odd parts of
-//     3 e.u + 9/2 (e.u)^2 - 3/2 u.u), so its large even part A = w (dl_c + rho_c Pe) is one
-//     value for both members and its rounding cancels in the momentum;
+//     3 e.u + 9/2 (e.u)^2 - 3/2 u.u); its large even part w (dl_c + rho_c Pe) is the same for
+//     both members and is subtracted from each population inside a multiply-add, never
+//     rounded on its own;
 //   * the Guo term Fb_a = w_a [3 (e_a - u).F + 9 (e_a.u)(e_a.F)] = Fe +- Fo likewise;
 //   * the MRT correction acts on the free rows through pair sums (even rows, one coefficient
 //     per pair class) and pair differences (odd rows);
@@ -256,37 +257,37 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
     constexpr int iw = L::c2(a) == 1 ? (Q == 9 ? 4 : 2) : 1;  // 36 w_a
     static_assert(iw / 36.0 - L::w(a) < 1e-15 && L::w(a) - iw / 36.0 < 1e-15);
     const R dp = pn[a] - pn[b];
-    const R dc = dp * ((pn[a] + pn[b]) - (R)2 * pn[0]);
+    const R dc = dp * fmx((R)-2, pn[0], pn[a] + pn[b]);
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       if (L::e(a, d) != 0) {
-        S1[d] += (R)(iw * L::e(a, d)) * dp;
-        S2[d] += (R)(iw * L::e(a, d)) * dc;
+        S1[d] = fmx((R)(iw * L::e(a, d)), dp, S1[d]);
+        S2[d] = fmx((R)(iw * L::e(a, d)), dc, S2[d]);
       }
     }
   });
   const R k1p = PC<R>::k1(P) * pn[0], k2 = PC<R>::k2(P);
   R F[3] = {0, 0, 0};
 #pragma unroll
-  for (int d = 0; d < D; ++d) F[d] = k1p * S1[d] + k2 * S2[d];
+  for (int d = 0; d < D; ++d) F[d] = fmx(k1p, S1[d], k2 * S2[d]);
 
   R rc[NC], rho = 0, gs = 0;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     rc[c] = PC<R>::rho_ref(P, c) + dl[c];
     rho += rc[c];
-    gs += PC<R>::gamma(P, c) * rc[c];
+    gs = fmx(PC<R>::gamma(P, c), rc[c], gs);
   }
   // barycentric velocity with the Guo half force
   R u[3] = {0, 0, 0};
   const R irho = (R)1 / rho;
 #pragma unroll
-  for (int d = 0; d < D; ++d) u[d] = (j[d] + (R)0.5 * F[d]) * irho;
+  for (int d = 0; d < D; ++d) u[d] = fmx((R)0.5, F[d], j[d]) * irho;
   R uu = 0, uF = 0;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    uu += u[d] * u[d];
-    uF += u[d] * F[d];
+    uu = fmx(u[d], u[d], uu);
+    uF = fmx(u[d], F[d], uF);
   }
   // Per pair p the even / odd parts of P_a = 3 e.u + 9/2 (e.u)^2 - 3/2 u.u (Pe +- Po) and of
   // Fb_a = w_a [3 (e_a - u).F + 9 (e_a.u)(e_a.F)] (Fe +- Fo) are formed inside each
@@ -304,7 +305,7 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
   };
   const R P0 = -(R)1.5 * uu;
   const R F0 = -(R)(3.0 * L::w(0)) * uF;
-  // per-pair values of the site (PT = 1): [0] w Pe, [1] 3 w e.u, [2] Fe, [3] Fo
+  // per-pair values of the site (PT = 1): [0] Pe, [1] e.u, [2] Fe, [3] Fo
   R pt_r[PT ? 4 * NP : 1];
   auto pt = [&](int i, int k) -> R& { return pt_r[PT ? i * NP + k : 0]; };
   if constexpr (PT) {
@@ -312,9 +313,9 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
       constexpr int a = L::pfirst(K);
       const R eu = dot(u, std::integral_constant<int, a>{});
       const R eF = dot(F, std::integral_constant<int, a>{});
-      pt(0, K) = (R)L::w(a) * ((R)4.5 * eu * eu + P0);
-      pt(1, K) = (R)(3.0 * L::w(a)) * eu;
-      pt(2, K) = (R)L::w(a) * ((R)9 * eu * eF - (R)3 * uF);
+      pt(0, K) = fmx((R)4.5 * eu, eu, P0);
+      pt(1, K) = eu;
+      pt(2, K) = (R)L::w(a) * fmx((R)9 * eu, eF, (R)-3 * uF);
       pt(3, K) = (R)(3.0 * L::w(a)) * eF;
     });
   }
@@ -369,34 +370,37 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
       opaque(uFo);
       opaque(P0o);
     };
-    // w_a dl_c per weight class (|e_a|^2 = 1, 2)
-    const R wdl1 = (R)L::w(L::pfirst(0)) * dl[C], wdl2 = (R)L::w(L::pfirst(NP - 1)) * dl[C];
+    // 3 w_a rho_c per weight class (|e_a|^2 = 1, 2)
+    const R b31 = (R)(3.0 * L::w(L::pfirst(0))) * rc[C], b32 = (R)(3.0 * L::w(L::pfirst(NP - 1))) * rc[C];
     static_assert(L::c2(L::pfirst(0)) == 1 && L::c2(L::pfirst(NP - 1)) == 2, "pair order");
+    // g_a,b = v_a,b - w (dl + rho Pe) -+ 3 w rho e.u: each member in two multiply-adds, so the
+    // large even part of the equilibrium is never rounded on its own. Rounding it first
+    // (one ulp of the population, a biased error because w is inexact in binary) measured a
+    // 6x larger error of the 20000-step FP32 droplet against the oracle.
     auto pair_g = [&](auto k_, R va, R vb, R& ga, R& gb, R& Fe, R& Fo) {
       constexpr int K = decltype(k_)::value;
       constexpr int a = L::pfirst(K);
+      R Pe, eu;
       if constexpr (PT) {
-        const R A = pt(0, K) * rc[C] + (L::c2(a) == 1 ? wdl1 : wdl2);
-        const R B = pt(1, K) * rc[C];
+        Pe = pt(0, K);
+        eu = pt(1, K);
         Fe = pt(2, K);
         Fo = pt(3, K);
-        ga = (va - A) - B;
-        gb = (vb - A) + B;
-        return;
+      } else {
+        eu = dot(uo, std::integral_constant<int, a>{});
+        const R eF = dot(Fo_, std::integral_constant<int, a>{});
+        Pe = fmx((R)4.5 * eu, eu, P0o);
+        Fe = (R)L::w(a) * fmx((R)9 * eu, eF, (R)-3 * uFo);
+        Fo = (R)(3.0 * L::w(a)) * eF;
       }
-      const R eu = dot(uo, std::integral_constant<int, a>{});
-      const R eF = dot(Fo_, std::integral_constant<int, a>{});
-      const R Pe = (R)4.5 * eu * eu + P0o;
-      Fe = (R)L::w(a) * ((R)9 * eu * eF - (R)3 * uFo);
-      Fo = (R)(3.0 * L::w(a)) * eF;
-      const R A = (R)L::w(a) * (dl[C] + rc[C] * Pe);
-      const R B = (R)(3.0 * L::w(a)) * rc[C] * eu;
-      ga = (va - A) - B;
-      gb = (vb - A) + B;
+      const R t = fmx(rc[C], Pe, dl[C]);
+      const R b3 = L::c2(a) == 1 ? b31 : b32;
+      ga = fmx(-b3, eu, fmx(-(R)L::w(a), t, va));
+      gb = fmx(b3, eu, fmx(-(R)L::w(a), t, vb));
     };
     const R v0 = (R)ld_pop(fc + AA<Q>::template rd<0, PAR>(P, so));
-    const R g0 = v0 - (R)L::w(0) * (dl[C] + rc[C] * P0);
-    R d0 = gkchi * F0 - om * g0;
+    const R g0 = fmx(-(R)L::w(0), fmx(rc[C], P0, dl[C]), v0);
+    R d0 = fmx(gkchi, F0, -om * g0);
     R lm[L::NK];
     if constexpr (MRT) {
       refresh();
@@ -409,25 +413,25 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
         R ga, gb, Fe, Fo;
         pair_g(std::integral_constant<int, K>{}, (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, so)),
                (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, so)), ga, gb, Fe, Fo);
-        cs[pclass<Q>(K)] += (ga + gb) + chi * Fe;
-        const R qm = (ga - gb) + chi * Fo;
+        cs[pclass<Q>(K)] += fmx(chi, Fe, ga + gb);
+        const R qm = fmx(chi, Fo, ga - gb);
         For<0, L::NK>::run([&]<int I>() {
           constexpr int k = L::krow(I);
           constexpr int c = L::m(k, a);
-          if constexpr (row_parity<Q>(k) == -1 && c != 0) mq[I] += (R)c * qm;
+          if constexpr (row_parity<Q>(k) == -1 && c != 0) mq[I] = fmx((R)c, qm, mq[I]);
         });
       });
       // lam_k (M q)_k over the free rows k
-      const R q0 = g0 + (R)0.5 * chi * F0;
+      const R q0 = fmx((R)0.5 * chi, F0, g0);
       For<0, L::NK>::run([&]<int I>() {
         constexpr int k = L::krow(I);
         R m = mq[I];
         if constexpr (row_parity<Q>(k) == 1) {
-          if constexpr (L::m(k, 0) != 0) m += (R)L::m(k, 0) * q0;
+          if constexpr (L::m(k, 0) != 0) m = fmx((R)L::m(k, 0), q0, m);
           For<1, 8>::run([&]<int CL>() {
             if constexpr (crep<Q>(CL) >= 0) {
               constexpr int c = L::m(k, L::pfirst(crep<Q>(CL)));
-              if constexpr (c != 0) m += (R)c * cs[CL];
+              if constexpr (c != 0) m = fmx((R)c, cs[CL], m);
             }
           });
         }
@@ -435,7 +439,7 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
       });
       For<0, L::NK>::run([&]<int I>() {
         constexpr int k = L::krow(I);
-        if constexpr (row_parity<Q>(k) == 1 && L::m(k, 0) != 0) d0 -= (R)L::m(k, 0) * lm[I];
+        if constexpr (row_parity<Q>(k) == 1 && L::m(k, 0) != 0) d0 = fmx(-(R)L::m(k, 0), lm[I], d0);
       });
       asm volatile("" ::: "memory");  // re-read the populations rather than keep them
     }
@@ -464,8 +468,8 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
           constexpr int a = L::pfirst(K), b = L::opp(a);
           R ga, gb, Fe, Fo;
           pair_g(std::integral_constant<int, K>{}, va[J], vb[J], ga, gb, Fe, Fo);
-          R da = gkchi * (Fe + Fo) - om * ga;
-          R db = gkchi * (Fe - Fo) - om * gb;
+          R da = fmx(gkchi, Fe + Fo, -om * ga);
+          R db = fmx(gkchi, Fe - Fo, -om * gb);
           if constexpr (MRT) {
             R ev = 0, od = 0;
             For<0, L::NK>::run([&]<int I>() {
@@ -473,9 +477,9 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
               constexpr int c = L::m(k, a);
               if constexpr (c != 0) {
                 if constexpr (row_parity<Q>(k) == 1)
-                  ev += (R)c * lm[I];
+                  ev = fmx((R)c, lm[I], ev);
                 else
-                  od += (R)c * lm[I];
+                  od = fmx((R)c, lm[I], od);
               }
             });
             da -= ev + od;
@@ -1069,7 +1073,7 @@ struct Launch {
       FusedArgs Ac = A;
       void* args[] = {(void*)&Pc, (void*)&fp, (void*)&st, (void*)&t_dev, (void*)&Ac};
       const size_t smem = 0;
-      return cudaLaunchCooperativeKernel((const void*)k_fused3<NC, Prec, MRT>, dim3((unsigned)(A.G / 2)),
+      return cudaLaunchCooperativeKernel((const void*)k_fused3<NC, Prec, MRT>, dim3((unsigned)(A.G / kF3WorkersPerCta)),
                                          dim3(kF3Threads), args, smem, s);
     }
   }
@@ -1096,7 +1100,7 @@ struct Launch {
     static const Ops ops = {psi,           collide,           fused,        fused_max_blocks, fused3,
                             fused3_max_blocks, init,          get_f,        set_f,            fields,
                             mass,          (int)sizeof(S),    (int)sizeof(PsiT), (int)sizeof(R), Fused<Q>::TX,
-                            Fused<Q>::TY,  Fused<Q>::P};
+                            Fused<Q>::TY,  Fused<Q>::P,       kF3WorkersPerCta,  kF3FlagSets};
     return &ops;
   }
 };

@@ -31,6 +31,8 @@ struct Ops {
   int fused_tx;     // fused-kernel tile: sites along x
   int fused_ty;     // and along y (1 for D2Q9)
   int fused_group;  // planes per synchronisation round
+  int fused3_wpc;   // plane-range kernel: workers per CTA
+  int fused3_flags; // and progress counters per worker
 };
 
 // one translation unit per lattice, storage type and collision
