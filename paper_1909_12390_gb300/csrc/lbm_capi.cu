@@ -901,7 +901,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
   const size_t sbytes = lbm_state_bytes(c), lbytes = (size_t)nc * Q * N * A->real_bytes;
   const unsigned nblk = (unsigned)((N + 255) / 256);
   std::vector<void*> snaps((size_t)K, nullptr);
-  void *la = nullptr, *lb = nullptr, *Fb = nullptr, *jb = nullptr, *rb = nullptr;
+  void *la = nullptr, *lb = nullptr, *Fb = nullptr, *jb = nullptr, *rb = nullptr, *psis = nullptr;
   double *gpart = nullptr, *kpart = nullptr, *dd = nullptr;
   int* st_s = nullptr;
   long long* t_s = nullptr;
@@ -910,6 +910,10 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
     if (e == cudaSuccess) e = cudaMalloc(p, b);
   };
   for (auto& p : snaps) alloc(&p, sbytes);
+  // psi of every state of a segment, computed once by the replay and read by the reverse steps
+  const size_t pbytes = (size_t)N * c->ops->psi_bytes;
+  alloc(&psis, (size_t)K * pbytes);
+  auto psi_of = [&](int i) { return (void*)((char*)psis + (size_t)i * pbytes); };
   alloc(&la, lbytes);
   alloc(&lb, lbytes);
   alloc(&Fb, (size_t)3 * N * A->real_bytes);
@@ -934,21 +938,25 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
   for (int k = nseg - 1; k >= 0 && e == cudaSuccess; --k) {
     const int64_t tk = c->rec_t0 + (int64_t)k * K;
     const int len = (int)std::min<int64_t>(K, c->rec_t0 + c->rec_n - tk);
-    // recompute the segment's states t_k .. t_k + len - 1 from its checkpoint
+    // recompute the segment's states t_k .. t_k + len - 1 from its checkpoint, keeping psi of
+    // each (state i - 1 is in snaps[i] before its step)
     e = cudaMemcpyAsync(snaps[0], c->ckpt[k], sbytes, cudaMemcpyDeviceToDevice, c->stream);
     for (int i = 1; i < len && e == cudaSuccess; ++i) {
       e = cudaMemcpyAsync(snaps[i], snaps[i - 1], sbytes, cudaMemcpyDeviceToDevice, c->stream);
       const int parity = (int)((tk + i - 1) & 1);
-      c->ops->psi(c->P, snaps[i], c->psi, st_s, parity, c->stream);
-      c->ops->collide(c->P, snaps[i], c->psi, st_s, t_s, parity, c->stream);
+      c->ops->psi(c->P, snaps[i], psi_of(i - 1), st_s, parity, c->stream);
+      c->ops->collide(c->P, snaps[i], psi_of(i - 1), st_s, t_s, parity, c->stream);
       if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      c->ops->psi(c->P, snaps[len - 1], psi_of(len - 1), st_s, (int)((tk + len - 1) & 1), c->stream);
+      e = cudaGetLastError();
     }
     // reverse steps
     for (int i = len - 1; i >= 0 && e == cudaSuccess; --i) {
       const int parity = (int)((tk + i) & 1);
-      c->ops->psi(c->P, snaps[i], c->psi, st_s, parity, c->stream);
-      A->pass_a(c->P, snaps[i], c->psi, la, Fb, jb, rb, parity, gpart, c->stream);
-      A->pass_b(c->P, snaps[i], c->psi, la, Fb, jb, rb, lb, parity, kpart, c->stream);
+      A->pass_a(c->P, snaps[i], psi_of(i), la, Fb, jb, rb, parity, gpart, c->stream);
+      A->pass_b(c->P, snaps[i], psi_of(i), la, Fb, jb, rb, lb, parity, kpart, c->stream);
       std::swap(la, lb);
       e = cudaGetLastError();
     }
@@ -965,6 +973,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hst, st_s, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   for (auto& p : snaps) cudaFree(p);
+  cudaFree(psis);
   cudaFree(la);
   cudaFree(lb);
   cudaFree(Fb);
