@@ -358,17 +358,19 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
     auto refresh = [&]() {
       so = s;
       opaque(so);
+      if constexpr (!PT) {  // with the table, u, F and u.F are not needed after it is filled
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        uo[d] = u[d];
-        Fo_[d] = F[d];
-        opaque(uo[d]);
-        opaque(Fo_[d]);
+        for (int d = 0; d < 3; ++d) {
+          uo[d] = u[d];
+          Fo_[d] = F[d];
+          opaque(uo[d]);
+          opaque(Fo_[d]);
+        }
+        uFo = uF;
+        P0o = P0;
+        opaque(uFo);
+        opaque(P0o);
       }
-      uFo = uF;
-      P0o = P0;
-      opaque(uFo);
-      opaque(P0o);
     };
     // 3 w_a rho_c per weight class (|e_a|^2 = 1, 2)
     const R b31 = (R)(3.0 * L::w(L::pfirst(0))) * rc[C], b32 = (R)(3.0 * L::w(L::pfirst(NP - 1))) * rc[C];
