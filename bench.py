@@ -421,6 +421,17 @@ def main():
     fus_ms, fus_n = gpu.profile_read(2)
     gpu.profile(False)
     mass_end = gpu.mass()
+    # S7, the per-component mass reduction (lbm_mass reads every population once), timed
+    # over 10 calls on the same stream; each call ends with a 3-double read-back
+    a7 = torch.cuda.Event(enable_timing=True)
+    b7 = torch.cuda.Event(enable_timing=True)
+    a7.record(stream)
+    for _ in range(10):
+        gpu.mass()
+    b7.record(stream)
+    torch.cuda.synchronize()
+    ms7 = a7.elapsed_time(b7) / 10
+    s7_bytes = N * 19 * nc * 4
     t_max = max_over_ranks(ms_total, dist, "cuda")
     ms_step = t_max / args.steps
     value = job_value(N, nc, args.steps, world, t_max)
@@ -514,6 +525,10 @@ def main():
                       "collision": "mrt", "precision": "fp32-shifted", "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs larger than L2 (%.2f GB populations)" % (N * 19 * nc * 4 / 1e9)},
            "e2e": e2e, "roofline": roof, "gpu_launches": psi_n + col_n + fus_n,
+           "mass_reduction": {"ms_per_call": ms7, "bytes": s7_bytes,
+                              "achieved_gbs": s7_bytes / (ms7 / 1e3) / 1e9,
+                              "frac": s7_bytes / (ms7 / 1e3) / 1e9 / peak,
+                              "note": "lbm_mass (S7) outside the timed step, 10 calls"},
            "clocks": clk.summary(), "site_mlups": value / nc,
            "mass_drift": float(np.max(np.abs(mass_end / (rho0.reshape(nc, -1).sum(1)) - 1)))}
     if variants:

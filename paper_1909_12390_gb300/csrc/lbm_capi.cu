@@ -20,7 +20,7 @@
 
 namespace lbm {
 
-__global__ void k_mass_final(const double* partial, int nblocks, int nc, double* out) {
+__global__ void k_mass_final(const double* partial, int nblocks, int nc, MassShift shift, double* out) {
   __shared__ double sh[256];
   for (int c = 0; c < nc; ++c) {
     double v = 0;
@@ -31,7 +31,7 @@ __global__ void k_mass_final(const double* partial, int nblocks, int nc, double*
       if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
       __syncthreads();
     }
-    if (threadIdx.x == 0) out[c] = sh[0];
+    if (threadIdx.x == 0) out[c] = sh[0] + shift.v[c];
     __syncthreads();
   }
 }

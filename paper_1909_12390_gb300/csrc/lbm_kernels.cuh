@@ -970,19 +970,42 @@ __global__ void k_fields(const Params P, const typename Prec::S* __restrict__ f,
     fields_body<Q, NC, Prec, 0>(P, f, psi, rho_out, u_out, p_out, psi_out, s);
 }
 
-// Per-component mass: per-block partial sums in FP64, then one block sums the partials,
-// both in a fixed order.
+// S7 per-component mass M_c = sum over sites and slots of the stored value, plus N rho_ref_c
+// (every slot of a component holds exactly one population in either AA layout, and the
+// shifts w_a rho_ref_c of one site's slots add up to rho_ref_c since sum_a w_a = 1; the
+// N rho_ref_c term is added once by k_mass_final). FP32 populations are summed per thread
+// with Knuth's TwoSum: a compensated FP32 sum, about 2^-48 relative, on the FP32 pipe (a
+// per-population conversion to FP64 would run on GB300's 1/64-rate FP64 pipe); FP64
+// populations are summed in FP64. Threads walk the sites with the fixed stride of a fixed grid
+// (kMassBlocks), and the blocks and k_mass_final reduce in FP64 in a fixed order, so the result
+// does not depend on scheduling.
+constexpr int kMassBlocks = 1024;
 template <int Q, int NC, class Prec>
 __global__ void __launch_bounds__(kBlock) k_mass_partial(const Params P, const typename Prec::S* __restrict__ f,
                                                          double* partial) {
   __shared__ double sh[kBlock];
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int c = 0; c < NC; ++c) {
+    const typename Prec::S* fc = f + (int64_t)c * Q * P.N;
     double v = 0;
-    if (idx < P.N) {
-      // every slot of the component holds exactly one population (in either AA layout, and
-      // opposite directions share a weight), so the slot-wise sum over the grid is the mass
-      for (int a = 0; a < Q; ++a) v += (double)f[((int64_t)c * Q + a) * P.N + idx] + Lat<Q>::w(a) * P.rho_ref[c];
+    if constexpr (sizeof(typename Prec::S) == 4) {
+      float hi = 0.f, lo = 0.f;
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += stride) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+          const float x = fc[(int64_t)a * P.N + i];
+          const float sm = hi + x;
+          const float bp = sm - hi;
+          lo += (hi - (sm - bp)) + (x - bp);
+          hi = sm;
+        }
+      }
+      v = (double)hi + (double)lo;
+    } else {
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += stride) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) v += (double)fc[(int64_t)a * P.N + i];
+      }
     }
     sh[threadIdx.x] = v;
     __syncthreads();
@@ -995,7 +1018,10 @@ __global__ void __launch_bounds__(kBlock) k_mass_partial(const Params P, const t
   }
 }
 
-__global__ void k_mass_final(const double* partial, int nblocks, int nc, double* out);
+struct MassShift {
+  double v[4];  // N rho_ref_c per component
+};
+__global__ void k_mass_final(const double* partial, int nblocks, int nc, MassShift shift, double* out);
 
 }  // namespace lbm
 
@@ -1094,9 +1120,11 @@ struct Launch {
                                                        parity);
   }
   static void mass(const Params& P, const void* f, double* partial, double* out, cudaStream_t s) {
-    unsigned nb = blocks(P);
+    const unsigned nb = std::min<unsigned>(blocks(P), (unsigned)kMassBlocks);  // partial holds blocks(P) rows
+    MassShift sh{};
+    for (int c = 0; c < NC; ++c) sh.v[c] = (double)P.N * P.rho_ref[c];
     k_mass_partial<Q, NC, Prec><<<nb, kBlock, 0, s>>>(P, (const S*)f, partial);
-    k_mass_final<<<1, kBlock, 0, s>>>(partial, (int)nb, NC, out);
+    k_mass_final<<<1, kBlock, 0, s>>>(partial, (int)nb, NC, sh, out);
   }
   static const Ops* table() {
     static const Ops ops = {psi,           collide,           fused,        fused_max_blocks, fused3,

@@ -324,3 +324,26 @@ def test_init_rejects_bad_densities_and_velocities(cases):
     gpu.step(2)
     assert gpu.time == 2
     gpu.close()
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32S])
+@pytest.mark.parametrize("key,shape", [("c3", (96, 96, 67)), ("c2", (1030, 601))])
+def test_mass_matches_exact_sum(cases, key, shape, precision):
+    """lbm_mass (S7: per-thread compensated FP32 sums or FP64 sums over a fixed grid stride,
+    FP64 block and final reductions in a fixed order, N rho_ref added once) against the exactly
+    rounded sum (math.fsum) of every population read back with lbm_get_f, after a few steps.
+    Both grids need several sites per thread and end in a ragged block; the result must also
+    repeat bit for bit."""
+    import math
+    c = cases[key]
+    grid = tuple(reversed(shape))
+    rho = lbm_inputs.ball_fields(grid, c["rho_l"], c["rho_v"], min(shape) / 4.0, 4.0)
+    gpu = gpu_lattice(c, shape, precision)
+    gpu.init(rho)
+    gpu.step(5)
+    f = gpu.get_f()
+    ref = np.array([math.fsum(f[s].ravel()) for s in range(f.shape[0])])
+    m = gpu.mass()
+    assert np.allclose(m, ref, rtol=1e-12, atol=0), (m, ref)
+    assert np.array_equal(gpu.mass(), m)
+    gpu.close()
