@@ -134,8 +134,11 @@ int64_t lbm_time(const lbm_ctx *ctx);
  * p[N] the EOS pressure (equal to the hydrodynamic pressure of Eq. hydropressure), psi[N]. */
 lbm_status lbm_fields(lbm_ctx *ctx, double *rho, double *u, double *p, double *psi);
 
-/* Total mass of each component, sum over sites of rho_s, reduced in FP64 in a fixed order
- * (bit-reproducible), into host mass[nc]. */
+/* Total mass of each component, sum over sites of rho_s (the step's S7 reduction), into host
+ * mass[nc]. FP32-shifted storage: each thread sums its populations with a compensated FP32
+ * sum (TwoSum, about 2^-48 relative) and the reference shift N rho_ref_s is added once; FP64
+ * storage sums in FP64. The grid and every reduction are fixed, so the result is
+ * bit-reproducible on a given device. Synchronous: returns after the copy to host. */
 lbm_status lbm_mass(lbm_ctx *ctx, double *mass);
 
 /* Current populations in the canonical FP64 layout f[nc][Q][N] (shift added back). */

@@ -383,8 +383,9 @@ bool setup_fused(lbm_ctx* c) {
 }
 
 // The path LBM_PATH_AUTO takes. D3Q19: the two-kernel step (measured on GB300 at 256^3 with
-// three FP32-shifted components: 2.4 ms against 3.6-4.1 ms for the fused forms, whose
-// collision runs at 14 warps per SM with register spills and per-plane synchronisation);
+// three FP32-shifted components: 2.15 ms against 3.4 ms for the plane-range fused form,
+// whose collision runs at 14 warps per SM with register spills and per-plane
+// synchronisation);
 // D2Q9: the tile-column fused step when it fits.
 bool setup_auto(lbm_ctx* c) {
   if (c->Q == 19) {
