@@ -118,7 +118,9 @@ lbm_status lbm_set_stream(lbm_ctx *ctx, void *stream);
 /* Sets the populations to the equilibrium of Eq. equilibrium(a), f_{s,a} = f_eq(rho_s, u),
  * from host arrays rho[nc][N] and u[3][N] (NULL: u = 0), and the step counter to 0.
  * With LBM_FP32_SHIFTED and rho_ref == NULL the shift references become the component minima
- * of rho. Densities must be finite and positive. */
+ * of rho. Densities must be finite and positive. Page-locked arrays (cudaHostAlloc,
+ * cudaHostRegister) are read in place by the kernels, others through a device copy; the call
+ * returns after the last read either way. */
 lbm_status lbm_init(lbm_ctx *ctx, const double *rho, const double *u);
 
 /* Advances n >= 0 steps. On a failing step the kernels of the remaining steps do nothing,
@@ -131,7 +133,9 @@ int64_t lbm_time(const lbm_ctx *ctx);
 
 /* Macroscopic fields of the current state into host arrays (any may be NULL):
  * rho[nc][N] cell-volume densities, u[3][N] barycentric velocity with the Guo half force,
- * p[N] the EOS pressure (equal to the hydrodynamic pressure of Eq. hydropressure), psi[N]. */
+ * p[N] the EOS pressure (equal to the hydrodynamic pressure of Eq. hydropressure), psi[N].
+ * Page-locked arrays are written in place by the kernel, others through a device copy; the
+ * call returns after the last write either way. */
 lbm_status lbm_fields(lbm_ctx *ctx, double *rho, double *u, double *p, double *psi);
 
 /* Total mass of each component, sum over sites of rho_s (the step's S7 reduction), into host

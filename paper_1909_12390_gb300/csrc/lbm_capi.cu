@@ -174,6 +174,29 @@ __global__ void k_check_init(const double* __restrict__ rho, const double* __res
   if (__any_sync(0xffffffffu, ubad) && (threadIdx.x & 31) == 0) atomicExch(&out[5], 1ull);
 }
 
+// Device address of the host range [p, p + n): non-null only when its first and last elements
+// both lie in page-locked memory mapped into the device's address space (cudaHostAlloc,
+// cudaHostRegister) at consistent addresses. The kernels then read or write the caller's
+// buffer directly over the host link, which on a Grace-Blackwell node is several times faster
+// than a copy-engine transfer of the same bytes; any other host memory is staged through
+// device memory by the caller.
+template <class T>
+T* mapped_range(T* p, size_t n) {
+  if (!p || n == 0) return nullptr;
+  auto dev = [](const void* q) -> const char* {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? (const char*)at.devicePointer : nullptr;
+  };
+  const char* a = dev(p);
+  const char* b = dev(p + (n - 1));
+  if (!a || !b || b - a != (ptrdiff_t)((n - 1) * sizeof(T))) return nullptr;
+  return (T*)a;
+}
+
 lbm_status sync_status(lbm_ctx* c) {
   int st = 0;
   long long t = 0;
@@ -643,8 +666,18 @@ lbm_status lbm_init(lbm_ctx* c, const double* rho, const double* u) {
   double* d_rho = c->scratch;
   double* d_u = c->scratch + (size_t)c->nc * N;
   unsigned long long* d_chk = (unsigned long long*)(c->scratch + (size_t)(c->nc + 5) * N);
-  CK(c, cudaMemcpyAsync(d_rho, rho, (size_t)c->nc * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  if (u) CK(c, cudaMemcpyAsync(d_u, u, (size_t)3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  // page-locked inputs are read in place by the kernels (this call synchronises before it
+  // returns); others are copied to device memory first
+  if (const double* m = mapped_range(rho, (size_t)c->nc * N))
+    d_rho = const_cast<double*>(m);
+  else
+    CK(c, cudaMemcpyAsync(d_rho, rho, (size_t)c->nc * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (u) {
+    if (const double* m = mapped_range(u, (size_t)3 * N))
+      d_u = const_cast<double*>(m);
+    else
+      CK(c, cudaMemcpyAsync(d_u, u, (size_t)3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  }
   // densities finite and > 0, u finite, and the component minima (the default FP32 shift)
   unsigned long long chk[6];
   CK(c, cudaMemsetAsync(d_chk, 0xff, 5 * sizeof(unsigned long long), c->stream));
@@ -755,14 +788,21 @@ lbm_status lbm_fields(lbm_ctx* c, double* rho, double* u, double* p, double* psi
   double* d_p = d_u + (size_t)3 * N;
   double* d_psi = d_p + N;
   const int parity = (int)(c->t & 1);
+  // page-locked outputs are written in place by the kernel (this call synchronises before it
+  // returns); others are staged in device memory and copied back
+  double* m_rho = mapped_range(rho, (size_t)c->nc * N);
+  double* m_u = mapped_range(u, (size_t)3 * N);
+  double* m_p = mapped_range(p, (size_t)N);
+  double* m_psi = mapped_range(psi, (size_t)N);
   if (u || psi) c->ops->psi(c->P, c->f, c->psi, c->status, parity, c->stream);  // the state's psi
-  c->ops->fields(c->P, c->f, c->psi, rho ? d_rho : nullptr, u ? d_u : nullptr, p ? d_p : nullptr,
-                 psi ? d_psi : nullptr, parity, c->stream);
+  c->ops->fields(c->P, c->f, c->psi, rho ? (m_rho ? m_rho : d_rho) : nullptr, u ? (m_u ? m_u : d_u) : nullptr,
+                 p ? (m_p ? m_p : d_p) : nullptr, psi ? (m_psi ? m_psi : d_psi) : nullptr, parity, c->stream);
   CK(c, cudaGetLastError());
-  if (rho) CK(c, cudaMemcpyAsync(rho, d_rho, (size_t)c->nc * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  if (u) CK(c, cudaMemcpyAsync(u, d_u, (size_t)3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  if (p) CK(c, cudaMemcpyAsync(p, d_p, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  if (psi) CK(c, cudaMemcpyAsync(psi, d_psi, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (rho && !m_rho)
+    CK(c, cudaMemcpyAsync(rho, d_rho, (size_t)c->nc * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (u && !m_u) CK(c, cudaMemcpyAsync(u, d_u, (size_t)3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (p && !m_p) CK(c, cudaMemcpyAsync(p, d_p, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (psi && !m_psi) CK(c, cudaMemcpyAsync(psi, d_psi, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   int64_t t = c->t;
   st = sync_status(c);
   c->t = t;
