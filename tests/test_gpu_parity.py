@@ -381,3 +381,32 @@ def test_page_locked_host_buffers_in_place(cases, precision):
             assert np.array_equal(fa[k], out[k]), k
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32S])
+@pytest.mark.parametrize("collision", [0, 1])
+@pytest.mark.parametrize("shape", [(1, 1), (2, 1), (1, 4), (3, 2), (1, 1, 1), (2, 1, 3), (1, 3, 2), (2, 2, 2)])
+def test_degenerate_grids(cases, shape, collision, precision):
+    """Axes of length 1 and 2, where the periodic stencil reaches the site itself or its one
+    neighbour twice: every density after 6 steps against the oracle, three components,
+    random densities and velocities; a step count of zero leaves the state and time alone."""
+    c = _mixture(cases, 3)
+    rates = cases["c2"]["mrt_s"] if len(shape) == 2 else cases["c3"]["mrt_s"]
+    ocase = oracle_case(c, shape, collision=collision, s=rates, tau=0.8, beta=1.9)
+    grid = ocase.grid
+    rho = random_rho(c, grid, seed=29)
+    u = 0.02 * (lbm_inputs.uniform01(7, 3 * ocase.nsites).reshape((3,) + grid) - 0.5)
+    if len(shape) == 2:
+        u[2] = 0
+    gpu = gpu_lattice(c, shape, precision, collision=collision, s=rates, tau=0.8, beta=1.9)
+    gpu.init(rho, u)
+    f0 = gpu.get_f()
+    gpu.step(0)
+    assert gpu.time == 0 and np.array_equal(gpu.get_f(), f0)
+    gpu.step(6)
+    f = oracle.step(ocase, oracle.equilibrium(ocase, rho, u), 6)
+    rg = gpu.fields()["rho"]
+    ro = oracle.fields(ocase, f).rho
+    assert gpu.time == 6
+    assert float(np.max(np.abs(rg - ro) / ro.sum(0))) < TOL[precision]
+    gpu.close()
