@@ -219,6 +219,51 @@ __device__ __forceinline__ void site_moments(const Params& P, const typename Pre
   });
 }
 
+// The two members of a pair of opposite populations pass through identical arithmetic. In
+// FP32 each such operation is one paired-FP32 instruction (fma / add / mul .f32x2 of
+// Blackwell) rather than two; each lane rounds exactly like the scalar operation it replaces,
+// so results do not change. FP64 (and LBM_COLLIDE_PACKED = 0) runs the two lanes as scalars.
+#ifndef LBM_COLLIDE_PACKED
+#define LBM_COLLIDE_PACKED 1
+#endif
+template <class R>
+struct V2 {
+  R x, y;
+};
+template <class R>
+__device__ __forceinline__ V2<R> v2(R a, R b) {
+  return {a, b};
+}
+__device__ __forceinline__ V2<float> fma2(V2<float> a, V2<float> b, V2<float> c) {
+#if LBM_COLLIDE_PACKED
+  const float2 r = __ffma2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y), make_float2(c.x, c.y));
+  return {r.x, r.y};
+#else
+  return {fmx(a.x, b.x, c.x), fmx(a.y, b.y, c.y)};
+#endif
+}
+__device__ __forceinline__ V2<float> add2(V2<float> a, V2<float> b) {
+#if LBM_COLLIDE_PACKED
+  const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+  return {r.x, r.y};
+#else
+  return {a.x + b.x, a.y + b.y};
+#endif
+}
+__device__ __forceinline__ V2<float> mul2(V2<float> a, V2<float> b) {
+#if LBM_COLLIDE_PACKED
+  const float2 r = __fmul2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+  return {r.x, r.y};
+#else
+  return {a.x * b.x, a.y * b.y};
+#endif
+}
+__device__ __forceinline__ V2<double> fma2(V2<double> a, V2<double> b, V2<double> c) {
+  return {fmx(a.x, b.x, c.x), fmx(a.y, b.y, c.y)};
+}
+__device__ __forceinline__ V2<double> add2(V2<double> a, V2<double> b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ V2<double> mul2(V2<double> a, V2<double> b) { return {a.x * b.x, a.y * b.y}; }
+
 // S4-S6 of one site given psi at the site (pn[0]) and its Q - 1 neighbours (pn[a] at x + e_a)
 // and the site's moments: total force, split, Guo-forced BGK or MRT collision, in-place AA
 // write. Everything is arranged over the pairs of opposite directions (a, b = opp(a)):
@@ -379,7 +424,7 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
     // large even part of the equilibrium is never rounded on its own. Rounding it first
     // (one ulp of the population, a biased error because w is inexact in binary) measured a
     // 6x larger error of the 20000-step FP32 droplet against the oracle.
-    auto pair_g = [&](auto k_, R va, R vb, R& ga, R& gb, R& Fe, R& Fo) {
+    auto pair_g = [&](auto k_, R va, R vb, V2<R>& g, R& Fe, R& Fo) {
       constexpr int K = decltype(k_)::value;
       constexpr int a = L::pfirst(K);
       R Pe, eu;
@@ -397,8 +442,8 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
       }
       const R t = fmx(rc[C], Pe, dl[C]);
       const R b3 = L::c2(a) == 1 ? b31 : b32;
-      ga = fmx(-b3, eu, fmx(-(R)L::w(a), t, va));
-      gb = fmx(b3, eu, fmx(-(R)L::w(a), t, vb));
+      const R mw = -(R)L::w(a);
+      g = fma2(v2(-b3, b3), v2(eu, eu), fma2(v2(mw, mw), v2(t, t), v2(va, vb)));
     };
     const R v0 = (R)ld_pop(fc + AA<Q>::template rd<0, PAR>(P, so));
     const R g0 = fmx(-(R)L::w(0), fmx(rc[C], P0, dl[C]), v0);
@@ -412,11 +457,14 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
       for (int i = 0; i < L::NK; ++i) mq[i] = 0;
       For<0, NP>::run([&]<int K>() {
         constexpr int a = L::pfirst(K), b = L::opp(a);
-        R ga, gb, Fe, Fo;
+        V2<R> g;
+        R Fe, Fo;
         pair_g(std::integral_constant<int, K>{}, (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, so)),
-               (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, so)), ga, gb, Fe, Fo);
-        cs[pclass<Q>(K)] += fmx(chi, Fe, ga + gb);
-        const R qm = fmx(chi, Fo, ga - gb);
+               (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, so)), g, Fe, Fo);
+        // {chi Fe + (g_a + g_b), chi Fo + (g_a - g_b)}
+        const V2<R> q = fma2(v2(chi, chi), v2(Fe, Fo), add2(v2(g.x, g.x), v2(g.y, -g.y)));
+        cs[pclass<Q>(K)] += q.x;
+        const R qm = q.y;
         For<0, L::NK>::run([&]<int I>() {
           constexpr int k = L::krow(I);
           constexpr int c = L::m(k, a);
@@ -468,10 +516,11 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
         constexpr int K = GI * G + J;
         if constexpr (K < NP) {
           constexpr int a = L::pfirst(K), b = L::opp(a);
-          R ga, gb, Fe, Fo;
-          pair_g(std::integral_constant<int, K>{}, va[J], vb[J], ga, gb, Fe, Fo);
-          R da = fmx(gkchi, Fe + Fo, -om * ga);
-          R db = fmx(gkchi, Fe - Fo, -om * gb);
+          V2<R> g;
+          R Fe, Fo;
+          pair_g(std::integral_constant<int, K>{}, va[J], vb[J], g, Fe, Fo);
+          // d = gk chi (Fe +- Fo) - omega g
+          V2<R> d = fma2(v2(gkchi, gkchi), add2(v2(Fe, Fe), v2(Fo, -Fo)), mul2(v2(-om, -om), g));
           if constexpr (MRT) {
             R ev = 0, od = 0;
             For<0, L::NK>::run([&]<int I>() {
@@ -484,11 +533,11 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
                   od = fmx((R)c, lm[I], od);
               }
             });
-            da -= ev + od;
-            db -= ev - od;
+            // d_a - (ev + od), d_b - (ev - od): the sums negated exactly
+            d = add2(d, add2(v2(-ev, -ev), v2(-od, od)));
           }
-          const R oa = va[J] + da;
-          const R ob = vb[J] + db;
+          const V2<R> o = add2(v2(va[J], vb[J]), d);
+          const R oa = o.x, ob = o.y;
           if constexpr (sizeof(R) == 4) rest -= oa + ob;
           store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<a, PAR>(P, so), oa);
           store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<b, PAR>(P, so), ob);
