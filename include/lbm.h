@@ -174,8 +174,8 @@ lbm_status lbm_restore(lbm_ctx *ctx, const void *buf, size_t bytes, int64_t t);
  *     divisible by the tile width (and ny by 8 for D3Q19) and the marched axis divisible
  *     into chunks of at least two groups of planes.
  * Both need all blocks co-resident. LBM_PATH_TWO_KERNEL runs a pseudo-potential pass and a
- * collide-stream pass. LBM_PATH_AUTO (the default at lbm_create) takes the two-kernel path for
- * D3Q19 (the faster one on GB300) and the fused path for D2Q9 when it fits. Setting LBM_PATH_FUSED on a grid it does not fit returns LBM_ERR_ARG and leaves the
+ * collide-stream pass. LBM_PATH_AUTO (the default at lbm_create) takes the two-kernel path, the
+ * faster one on GB300 for both lattices. Setting LBM_PATH_FUSED on a grid it does not fit returns LBM_ERR_ARG and leaves the
  * two-kernel path. All paths compute the same arithmetic in the same order per site, so their
  * results are bit-identical. */
 enum { LBM_PATH_AUTO = 0, LBM_PATH_TWO_KERNEL = 1, LBM_PATH_FUSED = 2 };

@@ -34,6 +34,27 @@ namespace lbm {
 
 constexpr int kAdjBlock = 256;
 
+// Adds the block-wide sums of v[0..M) to out[0..M) in a fixed order: warp shuffles, then the
+// warps' sums in warp order (red holds M * kAdjBlock / 32 doubles). Every thread of the block
+// calls it; the last one at the end of a kernel.
+template <int M>
+__device__ __forceinline__ void block_add(double (&v)[M], double* red, double* out) {
+  constexpr int W = kAdjBlock / 32;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    double x = v[m];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) red[m * W + (threadIdx.x >> 5)] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < M) {
+    double x = 0;
+    for (int w = 0; w < W; ++w) x += red[threadIdx.x * W + w];
+    out[threadIdx.x] += x;
+  }
+}
+
 template <int Q, int NC, class Prec, int PAR>
 __device__ __forceinline__ void load_site(const Params& P, const typename Prec::S* __restrict__ f, const Site& s,
                                           typename Prec::R (&rc)[NC], typename Prec::R (&j)[3]) {
@@ -67,7 +88,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_a(const Params P, const typen
   using R = typename Prec::R;
   using L = Lat<Q>;
   constexpr int D = L::D;
-  __shared__ double red[kAdjBlock];
+  __shared__ double red[NC * kAdjBlock / 32];
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double gg[NC];
 #pragma unroll
@@ -96,10 +117,11 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_a(const Params P, const typen
       rho += rc[c];
       gs += PC<R>::gamma(P, c) * rc[c];
     }
+    const R irho = (R)1 / rho, igs = (R)1 / gs;  // the divisions of this pass, once
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       F[d] = PC<R>::c1(P) * p0 * s1[d] + PC<R>::c2(P) * s2[d];
-      u[d] = (j[d] + (R)0.5 * F[d]) / rho;
+      u[d] = (j[d] + (R)0.5 * F[d]) * irho;
     }
     R uu = 0, uF = 0;
 #pragma unroll
@@ -111,7 +133,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_a(const Params P, const typen
     R ub[3] = {0, 0, 0}, Fd[3] = {0, 0, 0}, chib[NC], rb[NC], chi[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      chi[c] = PC<R>::gamma(P, c) * rc[c] / gs;
+      chi[c] = PC<R>::gamma(P, c) * rc[c] * igs;
       R L0 = 0, L1[3] = {0, 0, 0}, L2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
 #pragma unroll
       for (int a = 0; a < Q; ++a) {
@@ -157,27 +179,18 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_a(const Params P, const typen
     for (int c = 0; c < NC; ++c) cc += chib[c] * chi[c];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      rb[c] += -ubu / rho + PC<R>::gamma(P, c) * (chib[c] - cc) / gs;
-      gg[c] = (double)(rc[c] * (chib[c] - cc) / gs);
+      rb[c] += -ubu * irho + PC<R>::gamma(P, c) * (chib[c] - cc) * igs;
+      gg[c] = (double)(rc[c] * (chib[c] - cc) * igs);
       rbar[c * P.N + idx] = rb[c];
     }
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      Fbar[d * P.N + idx] = Fd[d] + ub[d] / ((R)2 * rho);
-      jbar[d * P.N + idx] = ub[d] / rho;
+      Fbar[d * P.N + idx] = Fd[d] + (R)0.5 * ub[d] * irho;
+      jbar[d * P.N + idx] = ub[d] * irho;
     }
   }
   // per-block partial sums of dL/dgamma, fixed order
-  for (int c = 0; c < NC; ++c) {
-    red[threadIdx.x] = gg[c];
-    __syncthreads();
-    for (int st = kAdjBlock / 2; st > 0; st >>= 1) {
-      if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) gpart[(int64_t)blockIdx.x * NC + c] += red[0];
-    __syncthreads();
-  }
+  block_add<NC>(gg, red, gpart + (int64_t)blockIdx.x * NC);
 }
 
 // Pass B: force / pseudo-potential / EOS adjoint and the new lam(t). kpart receives the
@@ -193,7 +206,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_b(const Params P, const typen
   using R = typename Prec::R;
   using L = Lat<Q>;
   constexpr int D = L::D;
-  __shared__ double red[kAdjBlock];
+  __shared__ double red[NC * NC * kAdjBlock / 32];
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double kg[NC * NC];
 #pragma unroll
@@ -222,32 +235,60 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_b(const Params P, const typen
     }
 #pragma unroll
     for (int d = 0; d < D; ++d) pb += PC<R>::c1(P) * Fbar[d * P.N + idx] * S1[d];
-    // psi = sqrt(psi2), psi2 = cpsi (p - rho / 3): the EOS derivative in FP64
-    const double psi2b = (double)pb / (2.0 * (double)p0);
-    const double pbar = P.cpsi * psi2b;
-    double n[NC], nt = 0, B = 0, A2 = 0, An[NC];
+    // psi = sqrt(psi2), psi2 = cpsi (p - rho / 3): the EOS derivative, in the arithmetic of
+    // the state (FP32 for FP32-shifted storage: its inputs carry FP32 precision and its terms
+    // cancel at most a few-fold, so it keeps about 7 digits, far inside what the gradient
+    // needs; GB300's FP64 pipe would make it the bottleneck of the reverse step). The zeta
+    // gradient is accumulated in FP64.
+    const R psi2b = pb / ((R)2 * p0);
+    const R pbar = PC<R>::cpsi(P) * psi2b;
+    auto cst = [&](const double& d, const float& f) -> R {
+      if constexpr (sizeof(R) == 4)
+        return f;
+      else
+        return d;
+    };
+    R n[NC], nt = 0, B = 0, A2 = 0, An[NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-      n[i] = (double)rc[i] * P.invM[i];
+      n[i] = rc[i] * PC<R>::invM(P, i);
       nt += n[i];
-      B += P.b[i] * n[i];
+      B += cst(P.b[i], P.b_f[i]) * n[i];
     }
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
       An[i] = 0;
 #pragma unroll
-      for (int k = 0; k < NC; ++k) An[i] += P.Qa[i * 4 + k] * n[k];
+      for (int k = 0; k < NC; ++k) An[i] += cst(P.Qa[i * 4 + k], P.Qa_f[i * 4 + k]) * n[k];
       A2 += n[i] * An[i];
     }
-    const double d1 = 1.0 - B, d2 = 1.0 + 2.0 * B - B * B;
+    const R d1 = (R)1 - B, d2 = (R)1 + (R)2 * B - B * B;
+    // dp/dn_i = RT/d1 + n RT b_i/d1^2 - 2 An_i/d2 + A2 (2 - 2B) b_i/d2^2, one division
+    const R RT = cst(P.RT, P.RT_f);
+    const R r12 = (R)1 / (d1 * d2);
+    const R id1 = d2 * r12, id2 = d1 * r12;
+    const R e0 = RT * id1;
+    const R eb = nt * RT * id1 * id1 + A2 * ((R)2 - (R)2 * B) * id2 * id2;
+    const R ea = (R)2 * id2;
+    const R t3 = pbar * (R)(1.0 / 3.0);
+    const R q = pbar * id2;
+    R ns[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) ns[i] = n[i] * cst(P.sa[i], P.sa_f[i]);
     R rb[NC];
+    R kgr[NC * NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-      const double dpdn = P.RT / d1 + nt * P.RT * P.b[i] / (d1 * d1) - 2.0 * An[i] / d2 +
-                          A2 * (2.0 - 2.0 * B) * P.b[i] / (d2 * d2);
-      rb[i] = rbar[i * P.N + idx] + (R)(pbar * dpdn * P.invM[i] - P.cpsi * psi2b / 3.0);
+      const R dpdn = e0 + eb * cst(P.b[i], P.b_f[i]) - ea * An[i];
+      rb[i] = rbar[i * P.N + idx] + (pbar * dpdn * PC<R>::invM(P, i) - t3);
 #pragma unroll
-      for (int k = 0; k < NC; ++k) kg[i * NC + k] = pbar * n[i] * n[k] * P.sa[i] * P.sa[k] / d2;
+      for (int k = 0; k < NC; ++k) kgr[i * NC + k] = q * ns[i] * ns[k];
+    }
+    if constexpr (sizeof(R) == 4) {
+      widen_all<NC * NC>(kgr, kg);
+    } else {
+#pragma unroll
+      for (int k = 0; k < NC * NC; ++k) kg[k] = kgr[k];
     }
     R jb[3] = {0, 0, 0};
 #pragma unroll
@@ -263,16 +304,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_b(const Params P, const typen
         lam_out[((int64_t)c * Q + a) * P.N + idx] = v;
       }
   }
-  for (int k = 0; k < NC * NC; ++k) {
-    red[threadIdx.x] = kg[k];
-    __syncthreads();
-    for (int st = kAdjBlock / 2; st > 0; st >>= 1) {
-      if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) kpart[(int64_t)blockIdx.x * NC * NC + k] += red[0];
-    __syncthreads();
-  }
+  block_add<NC * NC>(kg, red, kpart + (int64_t)blockIdx.x * NC * NC);
 }
 
 // lam(T)_sa(x) = dL/drho_s(x) for every a; dL/drho(0)_s(x) = sum_a w_a lam(0)_sa(x).

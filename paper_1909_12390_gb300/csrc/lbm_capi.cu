@@ -405,17 +405,14 @@ bool setup_fused(lbm_ctx* c) {
   return true;
 }
 
-// The path LBM_PATH_AUTO takes. D3Q19: the two-kernel step (measured on GB300 at 256^3 with
-// three FP32-shifted components: 2.15 ms against 3.4 ms for the plane-range fused form,
-// whose collision runs at 14 warps per SM with register spills and per-plane
-// synchronisation);
-// D2Q9: the tile-column fused step when it fits.
+// The path LBM_PATH_AUTO takes: the two-kernel step, the faster one measured on GB300 for
+// both lattices (D3Q19 at 256^3, three FP32-shifted components: 2.11 ms against 3.48 ms for
+// the plane-range fused form, whose collision runs at 14 warps per SM with register spills and
+// per-plane synchronisation; D2Q9 at 512^2, three components, MRT: 22.8 us against 33.5 us,
+// and at 256^2, two components, BGK: 8.2 us against 22.5 us for the tile-column form).
 bool setup_auto(lbm_ctx* c) {
-  if (c->Q == 19) {
-    free_fused(c);
-    return false;
-  }
-  return setup_fused(c);
+  free_fused(c);
+  return false;
 }
 
 // Progress counters must not exceed t * L when the step counter is reset or rewound.

@@ -192,6 +192,8 @@ struct Params {
   // psi^2 = cpsi RT (p / RT - rho / (3 RT))
   double sa_rt[4], Qa_rt[16];
   float cpsi_rt_f, c3rt_f;
+  // FP32 copies for the adjoint of FP32-shifted storage
+  float b_f[4], Qa_f[16], sa_f[4], RT_f;
 };
 
 // Fills the derived constants of P (call after any change of omega, lam, rho_ref, gamma,
@@ -218,6 +220,12 @@ inline void finalize_params(Params& P) {
     P.sa_rt[i] = P.RT > 0 ? P.sa[i] / std::sqrt(P.RT) : 0.0;
     for (int j = 0; j < 4; ++j) P.Qa_rt[i * 4 + j] = P.RT > 0 ? (i == j ? 1.0 : 2.0) * P.Qa[i * 4 + j] / P.RT : 0.0;
   }
+  for (int i = 0; i < 4; ++i) {
+    P.b_f[i] = (float)P.b[i];
+    P.sa_f[i] = (float)P.sa[i];
+  }
+  for (int i = 0; i < 16; ++i) P.Qa_f[i] = (float)P.Qa[i];
+  P.RT_f = (float)P.RT;
   P.cpsi_rt_f = (float)(P.cpsi * P.RT);
   P.c3rt_f = P.RT > 0 ? (float)(1.0 / (3.0 * P.RT)) : 0.0f;
 }
@@ -236,6 +244,8 @@ struct PC<double> {
   __device__ __forceinline__ static double lam(const Params& P, int i) { return P.lam[i]; }
   __device__ __forceinline__ static double rho_ref(const Params& P, int i) { return P.rho_ref[i]; }
   __device__ __forceinline__ static double gamma(const Params& P, int i) { return P.gamma[i]; }
+  __device__ __forceinline__ static double invM(const Params& P, int i) { return P.invM[i]; }
+  __device__ __forceinline__ static double cpsi(const Params& P) { return P.cpsi; }
 };
 template <>
 struct PC<float> {
@@ -248,6 +258,8 @@ struct PC<float> {
   __device__ __forceinline__ static float lam(const Params& P, int i) { return P.lam_f[i]; }
   __device__ __forceinline__ static float rho_ref(const Params& P, int i) { return P.rho_ref_f[i]; }
   __device__ __forceinline__ static float gamma(const Params& P, int i) { return P.gamma_f[i]; }
+  __device__ __forceinline__ static float invM(const Params& P, int i) { return P.invMf[i]; }
+  __device__ __forceinline__ static float cpsi(const Params& P) { return P.cpsi_f; }
 };
 
 // Status bits raised by kernels (OR-ed into one device word).
@@ -379,14 +391,14 @@ __device__ __forceinline__ EosOut<NC> eos_pr(const Params& P, const double (&rho
 // pipes. Each covers the common case exactly and reports whether it applies; callers fall back
 // to the conversion instruction, warp by warp, for the rest.
 //
-// Widening of a positive normal binary32 value (exact): the biased exponent gains
-// 1023 - 127 = 896 and the 23 fraction bits become the top 23 of the 52.
+// Widening of a normal binary32 value (exact): the sign carries over, the biased exponent
+// gains 1023 - 127 = 896 and the 23 fraction bits become the top 23 of the 52.
 __device__ __forceinline__ bool widen_int_ok(float x) {
-  return __float_as_uint(x) - 0x00800000u < 0x7f000000u;  // sign 0, biased exponent 1 .. 254
+  return (__float_as_uint(x) & 0x7fffffffu) - 0x00800000u < 0x7f000000u;  // biased exponent 1 .. 254
 }
 __device__ __forceinline__ double widen_int(float x) {
-  const unsigned u = __float_as_uint(x);
-  return __hiloint2double((int)((u >> 3) + 0x38000000u), (int)(u << 29));
+  const unsigned u = __float_as_uint(x), m = u & 0x7fffffffu;
+  return __hiloint2double((int)(((m >> 3) + 0x38000000u) | (u & 0x80000000u)), (int)(u << 29));
 }
 // Narrowing with round to nearest, ties to even, for |x| whose binary32 result is a normal
 // number or overflows to infinity: biased binary64 exponent 897 .. 1150. The 23 fraction bits
