@@ -32,7 +32,7 @@
 
 namespace lbm {
 
-constexpr int kAdjBlock = 256;
+constexpr int kAdjBlock = 256;  // 64 and 128 measured the same on the 256^2 adjoint workload
 
 // Adds the block-wide sums of v[0..M) to out[0..M) in a fixed order: warp shuffles, then the
 // warps' sums in warp order (red holds M * kAdjBlock / 32 doubles). Every thread of the block
@@ -335,6 +335,7 @@ struct AdjFns {  // same layout as the declaration in lbm_capi.cu
                  const void* rb, void* lam_out, int parity, double* kpart, cudaStream_t);
   void (*init_grad)(const Params&, const void* lam, double* drho0, cudaStream_t);
   int real_bytes;
+  int block;  // threads per block of the passes (the partial-sum arrays hold one row per block)
 };
 
 template <int Q, int NC, class Prec>
@@ -361,7 +362,7 @@ struct AdjLaunch {
     k_adj_init_grad<Q, NC, Prec><<<blocks(P), kAdjBlock, 0, s>>>(P, (const R*)lam, d);
   }
   static const AdjFns* table() {
-    static const AdjFns t = {seed, pass_a, pass_b, init_grad, (int)sizeof(R)};
+    static const AdjFns t = {seed, pass_a, pass_b, init_grad, (int)sizeof(R), kAdjBlock};
     return &t;
   }
 };

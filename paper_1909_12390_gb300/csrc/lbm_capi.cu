@@ -91,6 +91,7 @@ struct AdjFns {
                  const void* rb, void* lam_out, int parity, double* kpart, cudaStream_t);
   void (*init_grad)(const Params&, const void* lam, double* drho0, cudaStream_t);
   int real_bytes;
+  int block;  // threads per block of the passes (the partial-sum arrays hold one row per block)
 };
 const AdjFns* adj_fns(int Q, int nc, int precision);
 }  // namespace lbm
@@ -937,7 +938,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
   const int64_t N = c->P.N;
   const int nc = c->nc, Q = c->Q, K = c->ck_every;
   const size_t sbytes = lbm_state_bytes(c), lbytes = (size_t)nc * Q * N * A->real_bytes;
-  const unsigned nblk = (unsigned)((N + 255) / 256);
+  const unsigned nblk = (unsigned)((N + A->block - 1) / A->block);  // blocks of pass A / B
   std::vector<void*> snaps((size_t)K, nullptr);
   void *la = nullptr, *lb = nullptr, *Fb = nullptr, *jb = nullptr, *rb = nullptr, *psis = nullptr;
   double *gpart = nullptr, *kpart = nullptr, *dd = nullptr;
