@@ -973,33 +973,69 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
     A->seed(c->P, dd, la, c->stream);
     e = cudaGetLastError();
   }
+  // The work of one segment after its checkpoint is copied to snaps[0]: recompute states
+  // t_k + 1 .. t_k + len - 1, each step reading snaps[i - 1] and writing snaps[i], keeping psi
+  // of every state; then the reverse steps, which swap la and lb once each.
+  auto segment = [&](int64_t tk, int len, void*& la_, void*& lb_) {
+    cudaError_t r = cudaSuccess;
+    for (int i = 1; i < len && r == cudaSuccess; ++i) {
+      const int parity = (int)((tk + i - 1) & 1);
+      c->ops->psi(c->P, snaps[i - 1], psi_of(i - 1), st_s, parity, c->stream);
+      c->ops->collide_oop(c->P, snaps[i - 1], snaps[i], psi_of(i - 1), st_s, t_s, parity, c->stream);
+      r = cudaGetLastError();
+    }
+    if (r == cudaSuccess) {
+      c->ops->psi(c->P, snaps[len - 1], psi_of(len - 1), st_s, (int)((tk + len - 1) & 1), c->stream);
+      r = cudaGetLastError();
+    }
+    for (int i = len - 1; i >= 0 && r == cudaSuccess; --i) {
+      const int parity = (int)((tk + i) & 1);
+      A->pass_a(c->P, snaps[i], psi_of(i), la_, Fb, jb, rb, parity, gpart, c->stream);
+      A->pass_b(c->P, snaps[i], psi_of(i), la_, Fb, jb, rb, lb_, parity, kpart, c->stream);
+      std::swap(la_, lb_);
+      r = cudaGetLastError();
+    }
+    return r;
+  };
+  // Full segments repeat one launch sequence, which is captured as a graph per (parity of t_k,
+  // which buffer is la) and replayed; a failed capture falls back to direct launches.
+  cudaGraphExec_t gx[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  bool capture_ok = true;
+  void* const la0 = la;
   const int nseg = (int)c->ckpt.size();
   for (int k = nseg - 1; k >= 0 && e == cudaSuccess; --k) {
     const int64_t tk = c->rec_t0 + (int64_t)k * K;
     const int len = (int)std::min<int64_t>(K, c->rec_t0 + c->rec_n - tk);
-    // recompute the segment's states t_k .. t_k + len - 1 from its checkpoint, keeping psi of
-    // each (state i - 1 is in snaps[i] before its step)
     e = cudaMemcpyAsync(snaps[0], c->ckpt[k], sbytes, cudaMemcpyDeviceToDevice, c->stream);
-    for (int i = 1; i < len && e == cudaSuccess; ++i) {
-      e = cudaMemcpyAsync(snaps[i], snaps[i - 1], sbytes, cudaMemcpyDeviceToDevice, c->stream);
-      const int parity = (int)((tk + i - 1) & 1);
-      c->ops->psi(c->P, snaps[i], psi_of(i - 1), st_s, parity, c->stream);
-      c->ops->collide(c->P, snaps[i], psi_of(i - 1), st_s, t_s, parity, c->stream);
-      if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) break;
+    if (len == K && K > 1) {
+      cudaGraphExec_t& g = gx[tk & 1][la == la0 ? 0 : 1];
+      if (!g && capture_ok) {
+        void *a = la, *b = lb;
+        cudaGraph_t graph = nullptr;
+        capture_ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (capture_ok) {
+          const cudaError_t r = segment(tk, len, a, b);
+          capture_ok = cudaStreamEndCapture(c->stream, &graph) == cudaSuccess && r == cudaSuccess && graph &&
+                       cudaGraphInstantiate(&g, graph, 0) == cudaSuccess;
+          if (graph) cudaGraphDestroy(graph);
+        }
+        if (!capture_ok) {
+          g = nullptr;
+          cudaGetLastError();
+        }
+      }
+      if (g) {
+        e = cudaGraphLaunch(g, c->stream);
+        if (len & 1) std::swap(la, lb);
+        continue;
+      }
     }
-    if (e == cudaSuccess) {
-      c->ops->psi(c->P, snaps[len - 1], psi_of(len - 1), st_s, (int)((tk + len - 1) & 1), c->stream);
-      e = cudaGetLastError();
-    }
-    // reverse steps
-    for (int i = len - 1; i >= 0 && e == cudaSuccess; --i) {
-      const int parity = (int)((tk + i) & 1);
-      A->pass_a(c->P, snaps[i], psi_of(i), la, Fb, jb, rb, parity, gpart, c->stream);
-      A->pass_b(c->P, snaps[i], psi_of(i), la, Fb, jb, rb, lb, parity, kpart, c->stream);
-      std::swap(la, lb);
-      e = cudaGetLastError();
-    }
+    e = segment(tk, len, la, lb);
   }
+  for (auto& row : gx)
+    for (auto& g : row)
+      if (g) cudaGraphExecDestroy(g);
   if (e == cudaSuccess && drho0) {
     A->init_grad(c->P, la, dd, c->stream);
     e = cudaGetLastError();

@@ -282,7 +282,7 @@ __device__ __forceinline__ V2<double> mul2(V2<double> a, V2<double> b) { return 
 template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1, int PT = LBM_COLLIDE_PAIRS>
 __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S* __restrict__ f, const Site& s,
                                                const typename Prec::R (&pn)[Q], const typename Prec::R (&dl)[NC],
-                                               const typename Prec::R (&j)[3]) {
+                                               const typename Prec::R (&j)[3], typename Prec::S* fo = nullptr) {
   using R = typename Prec::R;
   using L = Lat<Q>;
   constexpr int D = L::D;
@@ -382,6 +382,9 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
     const R chi = chis[C];
     const R gkchi = gk * chi;
     typename Prec::S* fc = comp_base<Q>(f, P, C);
+    // the new values go to the same slots of fo when given (a step out of place: each site
+    // writes exactly the slots it reads), else in place
+    typename Prec::S* fcw = comp_base<Q>(fo ? fo : f, P, C);
     // Non-equilibrium part g = f - f_eq (stored variables) per pair: A is the even part of the
     // equilibrium (one value for both members), B the odd part; the BGK + Guo change is
     // d = gk chi Fb - omega g. For MRT a first pass accumulates the free-row moments of
@@ -539,8 +542,8 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
           const V2<R> o = add2(v2(va[J], vb[J]), d);
           const R oa = o.x, ob = o.y;
           if constexpr (sizeof(R) == 4) rest -= oa + ob;
-          store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<a, PAR>(P, so), oa);
-          store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<b, PAR>(P, so), ob);
+          store_pop<Prec, GLOBAL>(fcw + AA<Q>::template wr<a, PAR>(P, so), oa);
+          store_pop<Prec, GLOBAL>(fcw + AA<Q>::template wr<b, PAR>(P, so), ob);
         }
       });
     });
@@ -550,17 +553,17 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
     // mass (the mass row is not relaxed and sum_a Fb_a = 0), so in FP32 the rest population is
     // set from that invariant instead, leaving only unbiased rounding.
     const R out0 = sizeof(R) == 4 ? rest : v0 + d0;
-    store_pop<Prec, GLOBAL>(fc + AA<Q>::template wr<0, PAR>(P, s), out0);
+    store_pop<Prec, GLOBAL>(fcw + AA<Q>::template wr<0, PAR>(P, s), out0);
   });
 }
 
 // S1 and S4-S6 of one site (the moments, then the collision).
 template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1>
 __device__ __forceinline__ void site_collide(const Params& P, typename Prec::S* __restrict__ f, const Site& s,
-                                             const typename Prec::R (&pn)[Q]) {
+                                             const typename Prec::R (&pn)[Q], typename Prec::S* fo = nullptr) {
   typename Prec::R dl[NC], j[3];
   site_moments<Q, NC, Prec, PAR>(P, f, s, dl, j);
-  site_collide_m<Q, NC, Prec, MRT, PAR, GLOBAL>(P, f, s, pn, dl, j);
+  site_collide_m<Q, NC, Prec, MRT, PAR, GLOBAL>(P, f, s, pn, dl, j, fo);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -597,7 +600,8 @@ __global__ void __launch_bounds__(kBlock) k_psi(const Params P, const typename P
 // Pass 2: S4-S6 of every site; psi of the neighbours from global memory.
 template <int Q, int NC, class Prec, int MRT, int PAR>
 __device__ __forceinline__ void collide_body(const Params& P, typename Prec::S* __restrict__ f,
-                                             const typename Prec::PsiT* __restrict__ psi, int x) {
+                                             const typename Prec::PsiT* __restrict__ psi, int x,
+                                             typename Prec::S* fo = nullptr) {
   using R = typename Prec::R;
   using L = Lat<Q>;
   Site s;
@@ -606,7 +610,7 @@ __device__ __forceinline__ void collide_body(const Params& P, typename Prec::S* 
   pn[0] = (R)psi[s.idx];
 #pragma unroll
   for (int a = 1; a < Q; ++a) pn[a] = (R)psi[s.nb(P, L::e(a, 0), L::e(a, 1), L::e(a, 2))];
-  site_collide<Q, NC, Prec, MRT, PAR>(P, f, s, pn);
+  site_collide<Q, NC, Prec, MRT, PAR>(P, f, s, pn, fo);
 }
 
 template <int Q, int NC, class Prec, int MRT>
@@ -622,6 +626,23 @@ __global__ void __launch_bounds__(kCollideThreads, kCollideBlocks) k_collide(con
     collide_body<Q, NC, Prec, MRT, 1>(P, f, psi, x);
   else
     collide_body<Q, NC, Prec, MRT, 0>(P, f, psi, x);
+}
+
+// The collide pass out of place: reads the state in fin, writes the next one to fout (the
+// adjoint's replay keeps every state of a segment; the AA pattern makes the two buffers hold
+// the same slots, so fout needs no copy of fin first).
+template <int Q, int NC, class Prec, int MRT>
+__global__ void __launch_bounds__(kCollideThreads, kCollideBlocks)
+    k_collide_oop(const Params P, typename Prec::S* __restrict__ fin, typename Prec::S* __restrict__ fout,
+                  const typename Prec::PsiT* __restrict__ psi, const int* status, long long* t_dev, int parity) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= P.nx) return;
+  if (*(volatile const int*)status) return;
+  if (x == 0 && blockIdx.y == 0 && blockIdx.z == 0) *t_dev += 1;
+  if (parity)
+    collide_body<Q, NC, Prec, MRT, 1>(P, fin, psi, x, fout);
+  else
+    collide_body<Q, NC, Prec, MRT, 0>(P, fin, psi, x, fout);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1104,6 +1125,12 @@ struct Launch {
     site_grid(P, g, b, kCollideThreads);
     k_collide<Q, NC, Prec, MRT><<<g, b, 0, s>>>(P, (S*)f, (const PsiT*)ps, st, t_dev, parity);
   }
+  static void collide_oop(const Params& P, const void* fin, void* fout, const void* ps, const int* st,
+                          long long* t_dev, int parity, cudaStream_t s) {
+    dim3 g, b;
+    site_grid(P, g, b, kCollideThreads);
+    k_collide_oop<Q, NC, Prec, MRT><<<g, b, 0, s>>>(P, (S*)fin, (S*)fout, (const PsiT*)ps, st, t_dev, parity);
+  }
   static int fused_max_blocks() {
     int nb = 0, dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -1179,7 +1206,7 @@ struct Launch {
     static const Ops ops = {psi,           collide,           fused,        fused_max_blocks, fused3,
                             fused3_max_blocks, init,          get_f,        set_f,            fields,
                             mass,          (int)sizeof(S),    (int)sizeof(PsiT), (int)sizeof(R), Fused<Q>::TX,
-                            Fused<Q>::TY,  Fused<Q>::P,       kF3WorkersPerCta,  kF3FlagSets};
+                            Fused<Q>::TY,  Fused<Q>::P,       kF3WorkersPerCta,  kF3FlagSets,       collide_oop};
     return &ops;
   }
 };

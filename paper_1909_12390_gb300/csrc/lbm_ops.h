@@ -33,6 +33,9 @@ struct Ops {
   int fused_group;  // planes per synchronisation round
   int fused3_wpc;   // plane-range kernel: workers per CTA
   int fused3_flags; // and progress counters per worker
+  // the collide pass reading the state in fin and writing the next one to fout
+  void (*collide_oop)(const Params&, const void* fin, void* fout, const void* psi, const int* status,
+                      long long* t_dev, int parity, cudaStream_t);
 };
 
 // one translation unit per lattice, storage type and collision
