@@ -266,15 +266,25 @@ const char *lbm_batch_last_error(const lbm_batch *b);
  * arrays, FP64, or FP32 holding f - w_a rho_ref_s when eos->precision is LBM_FP32_SHIFTED
  * (eos->rho_ref gives the shift; NULL means 0), in the in-place streaming layout of step t0
  * (even t0: slot (x, a) holds f_a(x); lbm_save writes this layout). The other arguments are
- * those of lbm_create. On return *t_out (if not NULL) is the number of completed steps.
+ * those of lbm_create. On return *t_out (if not NULL) is the step index reached, t0 plus the
+ * number of steps completed: t0 + n on success, the index of the failing step otherwise (the
+ * populations then hold the state before that step).
  *
  * Scratch: the pseudo-potential, the status word and the step counter live in one fixed
  * device array inside the library, 256 B + LBM_STATIC_MAX_SITES * 8 B (8 MiB + 256 B), which
- * every GPU that loads the library holds until the process exits. Grids with more than
- * LBM_STATIC_MAX_SITES sites are rejected with LBM_ERR_ARG. The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress, with that device current); make that
- * first call before any stream capture. Every call shares the array and leaves its contents
- * behind; each call resets the status word and counter it uses. Calls whose work overlaps on
+ * a GPU holds from the moment the library's code is loaded on it until the process exits.
+ * Grids with more than LBM_STATIC_MAX_SITES sites are rejected with LBM_ERR_ARG.
+ * First use on a device: CUDA loads a library's device code lazily by default
+ * (CUDA_MODULE_LOADING=LAZY), so the first call on a device loads the code that holds the
+ * array, commits its 8 MiB and looks up its device address (cudaGetSymbolAddress, with that
+ * device current), and the first step of each lattice / precision / collision variant loads
+ * that variant's kernels. Loading reserves device memory and may synchronise the device. A
+ * caller that must not allocate later should therefore make one warm-up call that runs at
+ * least one step (n >= 1) of every variant it will use, at a point where allocation is
+ * allowed and before any stream capture; setting CUDA_MODULE_LOADING=EAGER before the
+ * process starts moves all of this to the loading of the library instead. After that, calls
+ * allocate nothing. Every call shares the array and leaves its contents behind; each call
+ * resets the status word and counter it uses. Calls whose work overlaps on
  * the GPU (other streams or threads on the same device) race on the array: serialise them.
  * The call synchronises `stream` (a cudaStream_t, NULL = default stream) before returning
  * the first failing step's status. lbm_step_static_error gives this thread's last message. */

@@ -16,11 +16,20 @@ from . import lbm
 
 
 def _gamma(spec, s):
-    g = np.array(spec["gamma"], dtype=float)
-    h = int(np.argmax(g == 1.0)) if "least_volatile" not in spec else int(spec["least_volatile"])
-    scale = np.full(len(g), float(s))
+    """(scaled gamma, unscaled gamma, least-volatile index h): gamma_i = s gamma0_i for i != h.
+    h is spec["least_volatile"], else the one entry of gamma0 equal to 1 (Eq. gamma normalises
+    the least volatile component's coefficient to 1)."""
+    g0 = np.array(spec["gamma"], dtype=float)
+    if "least_volatile" in spec:
+        h = int(spec["least_volatile"])
+    else:
+        ones = np.flatnonzero(g0 == 1.0)
+        if len(ones) != 1:
+            raise ValueError("spec needs 'least_volatile': gamma has %d entries equal to 1" % len(ones))
+        h = int(ones[0])
+    scale = np.full(len(g0), float(s))
     scale[h] = 1.0
-    return g * scale, h
+    return g0 * scale, g0, h
 
 
 def _kij(spec, zeta):
@@ -33,7 +42,7 @@ def _kij(spec, zeta):
 class LatticeRun(torch.autograd.Function):
     @staticmethod
     def forward(ctx, zeta, s, spec):
-        g, h = _gamma(spec, s.item())
+        g, g0, h = _gamma(spec, s.item())
         lat = lbm.Lattice(tuple(spec["shape"]), spec["components"], T=spec["T"], tau=spec["tau"], gamma=g,
                           kij=_kij(spec, zeta.item()), beta=spec["beta"], G=spec.get("G", -1.0),
                           precision=spec.get("precision", lbm.FP32_SHIFTED))
@@ -41,7 +50,7 @@ class LatticeRun(torch.autograd.Function):
         lat.record(spec["steps"], spec.get("checkpoint_every", 55))
         rho = lat.fields(u=False, p=False, psi=False)["rho"]
         ctx.lat = lat
-        ctx.gamma = g
+        ctx.gamma0 = g0
         ctx.h = h
         ctx.pair = spec.get("pair", (0, 1))
         return torch.from_numpy(rho)
@@ -51,6 +60,7 @@ class LatticeRun(torch.autograd.Function):
         dk, dg, _ = ctx.lat.adjoint(grad_rho.detach().cpu().numpy())
         i, j = ctx.pair
         dzeta = dk[i, j] + dk[j, i]
-        ds = sum(dg[k] * ctx.gamma[k] for k in range(len(dg)) if k != ctx.h) / 1.0
+        # gamma_k = s gamma0_k (k != h): dL/ds = sum_k dL/dgamma_k gamma0_k
+        ds = sum(dg[k] * ctx.gamma0[k] for k in range(len(dg)) if k != ctx.h)
         ctx.lat.close()
         return (torch.tensor(dzeta, dtype=torch.float64), torch.tensor(ds, dtype=torch.float64), None)

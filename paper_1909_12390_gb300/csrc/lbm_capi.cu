@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/lbm.h: argument validation, the Peng-Robinson
 // component parameters of Section 3.2, device allocation, the step loop (replayed from a
 // captured CUDA graph once it is long enough) and read-back.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -175,27 +176,54 @@ __global__ void k_check_init(const double* __restrict__ rho, const double* __res
   if (__any_sync(0xffffffffu, ubad) && (threadIdx.x & 31) == 0) atomicExch(&out[5], 1ull);
 }
 
-// Device address of the host range [p, p + n): non-null only when its first and last elements
-// both lie in page-locked memory mapped into the device's address space (cudaHostAlloc,
-// cudaHostRegister) at consistent addresses. The kernels then read or write the caller's
-// buffer directly over the host link, which on a Grace-Blackwell node is several times faster
-// than a copy-engine transfer of the same bytes; any other host memory is staged through
+// Allocation range [start, start + size) that the driver records for address p: the
+// cudaHostAlloc / cudaHostRegister range for page-locked host memory, the allocation for device
+// memory. The driver entry point is looked up through the runtime, so the library links no
+// driver library of its own. False when the driver knows no range for p.
+bool pointer_range(const void* p, uintptr_t* start, size_t* size) {
+  using Fn = CUresult (*)(void*, CUpointer_attribute, CUdeviceptr);
+  static Fn fn = []() -> Fn {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return (Fn)f;
+  }();
+  if (!fn) return false;
+  CUdeviceptr s0 = 0;
+  size_t n0 = 0;
+  if (fn(&s0, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, (CUdeviceptr)p) != CUDA_SUCCESS ||
+      fn(&n0, CU_POINTER_ATTRIBUTE_RANGE_SIZE, (CUdeviceptr)p) != CUDA_SUCCESS)
+    return false;
+  *start = (uintptr_t)s0;
+  *size = n0;
+  return true;
+}
+
+// Device address of the host range [p, p + n): non-null only when the whole range lies inside
+// one page-locked allocation mapped into the device's address space (cudaHostAlloc,
+// cudaHostRegister). The kernels then read or write the caller's buffer directly over the
+// host link, which on a Grace-Blackwell node is several times faster than a copy-engine
+// transfer of the same bytes; any other host memory (including a range that runs past its
+// registration into unregistered memory, or across two registrations) is staged through
 // device memory by the caller.
 template <class T>
 T* mapped_range(T* p, size_t n) {
   if (!p || n == 0) return nullptr;
-  auto dev = [](const void* q) -> const char* {
-    cudaPointerAttributes at{};
-    if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    return at.type == cudaMemoryTypeHost ? (const char*)at.devicePointer : nullptr;
-  };
-  const char* a = dev(p);
-  const char* b = dev(p + (n - 1));
-  if (!a || !b || b - a != (ptrdiff_t)((n - 1) * sizeof(T))) return nullptr;
-  return (T*)a;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+  uintptr_t start = 0;
+  size_t size = 0;
+  const uintptr_t a = (uintptr_t)p;
+  if (!pointer_range(p, &start, &size) || a < start || n > (start + size - a) / sizeof(T)) return nullptr;
+  return (T*)at.devicePointer;
 }
 
 lbm_status sync_status(lbm_ctx* c) {

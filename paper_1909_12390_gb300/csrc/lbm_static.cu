@@ -90,6 +90,9 @@ lbm_status lbm_step_static(const lbm_grid* grid, int nc, const lbm_component* co
   if (t_out) *t_out = ht;
   if (hs & lbm::ST_NONFINITE) return say(LBM_ERR_NONFINITE, "non-finite density or psi^2");
   if (hs & lbm::ST_PSI_DOMAIN) return say(LBM_ERR_PSI_DOMAIN, "psi^2 < 0 or b_m n >= 1");
+  // any other status bit (none of the two-kernel step's kernels raises one today) is reported
+  // as the context path reports it, never as success
+  if (hs) return say(LBM_ERR_TIMEOUT, "device status bits set");
   return LBM_OK;
 }
 

@@ -194,14 +194,17 @@ def make_args(shape, components, T, gamma=None, kij=None, beta=1.0, G=-1.0, coll
 
 def step_static(shape, components, T, tau, f_device_ptr: int, t0: int, n: int, stream: int = 0, **kw):
     """lbm_step_static on caller-owned device populations at address f_device_ptr; returns the
-    number of completed steps. Raises LBMError on failure."""
+    step index reached (t0 + completed steps). Raises LBMError on failure; its `time` attribute
+    is then the index of the failing step (None when the call failed before running)."""
     grid, comps, eos, keep = make_args(shape, components, T, **kw)
     tout = ctypes.c_int64()
     st = lib().lbm_step_static(ctypes.byref(grid), len(components), comps, ctypes.byref(eos), tau,
                                ctypes.c_void_p(f_device_ptr), int(t0), int(n), ctypes.c_void_p(stream or None),
                                ctypes.byref(tout))
     if st != OK:
-        raise LBMError(st, lib().lbm_step_static_error().decode())
+        err = LBMError(st, lib().lbm_step_static_error().decode())
+        err.time = tout.value if st in (ERR_PSI_DOMAIN, ERR_NONFINITE, ERR_TIMEOUT) else None
+        raise err
     return tout.value
 
 

@@ -47,15 +47,16 @@ def _gpu_run(c, shape, rho0, precision, k12, s, steps, K):
     return lat, g
 
 
-def _oracle_grads(c, shape, rho0, w, k12, steps):
-    g = np.array(c["gamma"])
+def _oracle_grads(c, shape, rho0, w, k12, steps, s=1.0):
+    g0 = np.array(c["gamma"])
+    g = g0 * np.array([s, 1.0])
     oc = oracle_case(dict(c, Q=9), shape, collision=0, kij=[[0.0, k12], [k12, 0.0]], gamma=list(g))
     f0 = oracle.equilibrium(oc, rho0)
     df0 = np.zeros((2,) + f0.shape)
     dk = np.zeros((2, 2, 2))
     dk[0, 0, 1] = dk[0, 1, 0] = 1.0          # direction 0: d/dk12
     dg = np.zeros((2, 2))
-    dg[1, 0] = g[0]                           # direction 1: d/ds, gamma_0 = s g_0
+    dg[1, 0] = g0[0]                          # direction 1: d/ds, gamma_0 = s g0_0
     f, df = oracle.step_dual(oc, f0, df0, dk, dg, steps)
     rho = f.sum(axis=1)
     drho = df.sum(axis=2)
@@ -63,20 +64,20 @@ def _oracle_grads(c, shape, rho0, w, k12, steps):
     return L, float(np.sum(gl * drho[0])), float(np.sum(gl * drho[1])), rho
 
 
-@pytest.mark.parametrize("K", [7, 1, 60])
-def test_adjoint_fp64_matches_oracle_duals(case5, K):
+@pytest.mark.parametrize("K,s", [(7, 1.0), (1, 1.0), (60, 1.0), (7, 1.3)])
+def test_adjoint_fp64_matches_oracle_duals(case5, K, s):
     c = case5
     shape = (32, 24)
     steps = 60
     rho0, w = _setup(c, shape, 6.0)
     k12 = 0.01
-    lat, g = _gpu_run(c, shape, rho0, FP64, k12, 1.0, steps, K)
+    lat, g = _gpu_run(c, shape, rho0, FP64, k12, s, steps, K)
     rho = lat.fields(u=False, p=False, psi=False)["rho"]
     L, gl = _loss_grad(rho, w)
     dk, dgam, d0 = lat.adjoint(gl)
     dk12 = dk[0, 1] + dk[1, 0]
-    ds = dgam[0] * g[0]
-    Lo, ok12, os_, rho_o = _oracle_grads(c, shape, rho0, w, k12, steps)
+    ds = dgam[0] * c["gamma"][0]  # gamma_0 = s gamma0_0
+    Lo, ok12, os_, rho_o = _oracle_grads(c, shape, rho0, w, k12, steps, s)
     assert np.max(np.abs(rho - rho_o) / rho_o) < 1e-11
     print("K=%d dL/dk12 %.12e (oracle %.12e)  dL/ds %.12e (oracle %.12e)" % (K, dk12, ok12, ds, os_))
     assert dk12 == pytest.approx(ok12, rel=1e-8)
@@ -123,8 +124,10 @@ def test_adjoint_fp32_matches_fp64_oracle(case5):
     assert dgam[0] * g[0] == pytest.approx(os_, rel=2e-3)
 
 
-def test_autograd_function_gradients(case5):
-    """torch.autograd.Function wrapper: backward gives the same gradients as the C ABI."""
+@pytest.mark.parametrize("s0", [1.0, 1.3])
+def test_autograd_function_gradients(case5, s0):
+    """torch.autograd.Function wrapper: its gradients equal the oracle's dual numbers, also at
+    a split-factor scale s != 1 (dL/ds = sum_k dL/dgamma_k gamma0_k, not s times that)."""
     import torch
     from paper_1909_12390_gb300 import lbm
     from paper_1909_12390_gb300.autograd import LatticeRun
@@ -135,11 +138,11 @@ def test_autograd_function_gradients(case5):
                 beta=c["beta"], G=c["G"], steps=30, checkpoint_every=8, rho0=rho0, precision=lbm.FP64,
                 pair=(0, 1), least_volatile=1)
     zeta = torch.tensor(0.01, dtype=torch.float64, requires_grad=True)
-    s = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    s = torch.tensor(s0, dtype=torch.float64, requires_grad=True)
     rho = LatticeRun.apply(zeta, s, spec)
     loss = 0.5 * (torch.from_numpy(w) * rho * rho).sum()
     loss.backward()
-    _, ok12, os_, _ = _oracle_grads(c, shape, rho0, w, 0.01, 30)
+    _, ok12, os_, _ = _oracle_grads(c, shape, rho0, w, 0.01, 30, s0)
     assert zeta.grad.item() == pytest.approx(ok12, rel=1e-8)
     assert s.grad.item() == pytest.approx(os_, rel=1e-8)
 

@@ -383,6 +383,46 @@ def test_page_locked_host_buffers_in_place(cases, precision):
         b.close()
 
 
+def test_host_range_straddling_a_registration_is_staged(cases):
+    """A host array whose first part lies in a page-locked registration (cudaHostRegister) and
+    whose rest lies in unregistered memory is not read in place (the library checks that the
+    whole range lies in one registration): lbm_init and lbm_fields give the pageable path's
+    results bit for bit."""
+    torch = pytest.importorskip("torch")
+    c = cases["c3"]
+    shape = (24, 20, 18)
+    grid = tuple(reversed(shape))
+    rho = lbm_inputs.ball_fields(grid, c["rho_l"], c["rho_v"], 6.0, 4.0)
+    n = rho.size
+    big = np.zeros(2 * n)
+    half = big.ctypes.data + 8 * (n // 2)
+    page = 1 << 16
+    start = (big.ctypes.data + page - 1) // page * page
+    length = (half - start) // page * page
+    assert length > 0
+    cudart = torch.cuda.cudart()
+    assert int(cudart.cudaHostRegister(start, length, 0)) == 0
+    try:
+        k = (start - big.ctypes.data) // 8 + 8  # range starts inside the registration, ends past it
+        view = big[k:k + n].reshape(rho.shape)
+        view[...] = rho
+        a = gpu_lattice(c, shape, FP64)
+        b = gpu_lattice(c, shape, FP64)
+        a.init(rho)
+        b.init(view)
+        assert np.array_equal(a.get_f(), b.get_f())
+        a.step(2)
+        b.step(2)
+        want = a.fields()["rho"]
+        view[...] = 0.0
+        b.fields_into(rho=view)
+        assert np.array_equal(view, want)
+        a.close()
+        b.close()
+    finally:
+        cudart.cudaHostUnregister(start)
+
+
 @pytest.mark.parametrize("precision", [FP64, FP32S])
 @pytest.mark.parametrize("collision", [0, 1])
 @pytest.mark.parametrize("shape", [(1, 1), (2, 1), (1, 4), (3, 2), (1, 1, 1), (2, 1, 3), (1, 3, 2), (2, 2, 2)])
