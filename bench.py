@@ -34,6 +34,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "component-MLUPS (D3Q19 MRT, FP32-shifted populations, FP64 EOS)"
+PATH_NAMES = {1: "two-kernel", 2: "fused", 3: "trailing"}
+# what the FP32-shifted path computes in which precision
+EOS_PRECISION = ("FP64: the EOS sums B, A2, the numerator and denominator of p (their cancellation); "
+                 "FP32: n_i = rho_i / M_i, the quotient p = pD / Dd, psi = sqrt(psi^2), moments, force, collision; "
+                 "mass (S7): compensated FP32 sums per thread reduced in FP64")
 UNIT = "MLUPS/component"
 WORKLOAD = "sphere_d3q19_fp32s_mrt: 3 components C1/C3/nC5, 256^3 periodic, droplet R=48"
 
@@ -306,7 +311,7 @@ def l2_variants(stream, steps=2000):
         b.record(stream)
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / steps
-        path = "fused" if g.path == lbm.PATH_FUSED else "two-kernel"
+        path = PATH_NAMES[g.path]
         g.close()
         nc, n = len(c["components"]), int(np.prod(c["shape"]))
         q = 19 if len(c["shape"]) == 3 else 9
@@ -327,14 +332,7 @@ def batched_variant(stream, steps=1000):
     from paper_1909_12390_gb300 import lbm
     with open(os.path.join(ROOT, "tests", "golden", "cases.json")) as fh:
         sw = json.load(fh)["c4"]
-    specs, rhos = [], []
-    for c in sw["cases"]:
-        nx, ny = c["shape"]
-        ini = c["init"]
-        rhos.append(lbm_inputs.slab_fields((ny, nx), c["rho_l"], c["rho_v"], ini["lo"], ini["hi"], ini["width"],
-                                           ini["noise"], ini["seed"], axis=1))
-        specs.append(dict(shape=c["shape"], components=[(d["Tc"], d["pc"], d["omega"], d["M"]) for d in c["components"]],
-                          T=c["T"], tau=sw["tau"], gamma=c["gamma"], kij=np.array(c["kij"]), beta=sw["beta"], G=c["G"]))
+    specs, rhos = _sweep_specs(sw)
     b = lbm.Batch(specs, precision=lbm.FP32_SHIFTED)
     b.init(rhos)
     report = b.tune(20)
@@ -350,6 +348,223 @@ def batched_variant(stream, steps=1000):
             "tune": report}
 
 
+def _load_refs():
+    p = os.path.join(ROOT, "tests", "golden", "long_runs.npz")
+    return dict(np.load(p)) if os.path.exists(p) else {}
+
+
+def config_checks():
+    """Every workload at its stated step count on the library's automatic path against the
+    stored FP64 oracle runs (tests/golden/long_runs.npz, written by the committed script beside
+    it from oracle/ only). Error measure: max over the compared sites and components of
+    |rho_s - rho_s,oracle| / sum_s rho_s,oracle (FP64: / rho_s,oracle)."""
+    from paper_1909_12390_gb300 import lbm
+    ref = _load_refs()
+    out = {}
+
+    def err(got, want, fp64):
+        return float(np.max(np.abs(got - want) / (want if fp64 else want.sum(0))))
+
+    def run(c, shape, precision, steps, rho0):
+        g = lattice_for(dict(c, shape=list(shape)), precision)
+        g.init(rho0)
+        t0 = time.perf_counter()
+        g.step(steps)
+        el = time.perf_counter() - t0
+        rho = g.fields(u=False, p=False, psi=False)["rho"]
+        m = g.mass()
+        path = PATH_NAMES[g.path]
+        g.close()
+        return rho, m, el, path
+
+    if "slab_rho" in ref:
+        c = load_case("c1")
+        rho, m, el, path = run(c, c["shape"], lbm.FP64, int(ref["slab_steps"]), case_fields(c))
+        out["c1_slab"] = {"steps": int(ref["slab_steps"]), "err": err(rho, ref["slab_rho"], True), "tolerance": 1e-10,
+                          "compared": "every site", "mass_rel_err": float(np.max(np.abs(m / ref["slab_mass"] - 1))),
+                          "path": path, "host_s": el}
+    if "droplet_rho" in ref:
+        c = load_case("c2")
+        rho, m, el, path = run(c, c["shape"], lbm.FP32_SHIFTED, int(ref["droplet_steps"]), case_fields(c))
+        ys, xs = ref["droplet_sites"]
+        out["c2_droplet"] = {"steps": int(ref["droplet_steps"]), "err": err(rho[:, ys, xs], ref["droplet_rho"], False),
+                             "tolerance": 2e-4, "compared": "%d sampled sites" % len(ys),
+                             "mass_rel_err": float(np.max(np.abs(m / ref["droplet_mass"] - 1))), "path": path,
+                             "host_s": el}
+    if "sphere_rho" in ref:
+        c = load_case("c3")
+        shape = [int(v) for v in ref["sphere_shape"]]
+        cc = dict(c, shape=shape, init=dict(c["init"], radius=float(ref["sphere_radius"])))
+        rho, m, el, path = run(cc, shape, lbm.FP32_SHIFTED, int(ref["sphere_steps"]), init_fields(cc))
+        zs, ys, xs = ref["sphere_sites"]
+        out["c3_sphere"] = {"steps": int(ref["sphere_steps"]), "grid": shape, "radius": float(ref["sphere_radius"]),
+                            "err": err(rho[:, zs, ys, xs], ref["sphere_rho"], False), "tolerance": 2e-4,
+                            "compared": "%d sampled sites" % len(zs),
+                            "mass_rel_err": float(np.max(np.abs(m / ref["sphere_mass"] - 1))), "path": path,
+                            "host_s": el,
+                            "note": "the 256^3 workload's mixture, state and liquid fraction on the box the oracle "
+                                    "can step 5000 times"}
+    if "sweep_cases" in ref:
+        with open(os.path.join(ROOT, "tests", "golden", "cases.json")) as fh:
+            sw = json.load(fh)["c4"]
+        specs, rhos = _sweep_specs(sw)
+        b = lbm.Batch(specs, precision=lbm.FP32_SHIFTED)
+        b.init(rhos)
+        b.tune(20)
+        b.init(rhos)
+        t0 = time.perf_counter()
+        b.step(int(ref["sweep_steps"]))
+        el = time.perf_counter() - t0
+        got = b.rho()
+        b.close()
+        e = max(err(got[i], ref["sweep_rho_%d" % i], False) for i in ref["sweep_cases"])
+        out["c4_sweep"] = {"steps": int(ref["sweep_steps"]), "err": e, "tolerance": 2e-4,
+                           "compared": "every site of cases %s" % list(map(int, ref["sweep_cases"])),
+                           "cases": len(specs), "host_s": el}
+    if "adjoint_rho" in ref:
+        c = load_case("c5")
+        grid = tuple(reversed(c["shape"]))
+        rho0 = init_fields_ball(c, grid)
+        rho, m, el, path = run(c, c["shape"], lbm.FP32_SHIFTED, int(ref["adjoint_steps"]), rho0)
+        ys, xs = ref["adjoint_sites"]
+        out["c5_adjoint_droplet"] = {"steps": int(ref["adjoint_steps"]),
+                                     "err": err(rho[:, ys, xs], ref["adjoint_rho"], False), "tolerance": 2e-4,
+                                     "compared": "%d sampled sites (the forward run of the adjoint workload)" % len(ys),
+                                     "path": path, "host_s": el}
+    return out
+
+
+def init_fields_ball(c, grid):
+    import lbm_inputs
+    return lbm_inputs.ball_fields(grid, c["rho_l"], c["rho_v"], c["init"]["radius"], 4.0)
+
+
+def _sweep_specs(sw):
+    import lbm_inputs
+    specs, rhos = [], []
+    for c in sw["cases"]:
+        nx, ny = c["shape"]
+        ini = c["init"]
+        rhos.append(lbm_inputs.slab_fields((ny, nx), c["rho_l"], c["rho_v"], ini["lo"], ini["hi"], ini["width"],
+                                           ini["noise"], ini["seed"], axis=1))
+        specs.append(dict(shape=c["shape"], components=[(d["Tc"], d["pc"], d["omega"], d["M"]) for d in c["components"]],
+                          T=c["T"], tau=sw["tau"], gamma=c["gamma"], kij=np.array(c["kij"]), beta=sw["beta"], G=c["G"]))
+    return specs, rhos
+
+
+def adjoint_variant():
+    """The adjoint workload as stated (D2Q9 BGK binary droplet 256^2, FP32 forward, FP64 EOS,
+    3000 steps, checkpoints every 55 steps, loss on the bulk compositions and the density
+    profile against a target run at zeta_12 = 0.02; gradient with respect to zeta_12 and the
+    split-factor scale at zeta_12 = 0, s = 1) through LatticeRun and loss.backward(), host clock
+    around each call (each synchronises). Reports (recorded forward + backward) / plain forward
+    and the gradients against the FP64 oracle's dual numbers (stored run)."""
+    import torch
+
+    from paper_1909_12390_gb300 import lbm
+    from paper_1909_12390_gb300.autograd import LatticeRun
+    from paper_1909_12390_gb300.losses import composition_profile_loss
+    c = load_case("c5")
+    ref = _load_refs()
+    shape = tuple(c["shape"])
+    rho0 = init_fields_ball(c, tuple(reversed(shape)))
+    comps = [(d["Tc"], d["pc"], d["omega"], d["M"]) for d in c["components"]]
+    kt = float(c["target_k12"])
+    g = lbm.Lattice(shape, comps, T=c["T"], tau=c["tau"], gamma=c["gamma"], kij=np.array([[0.0, kt], [kt, 0.0]]),
+                    beta=c["beta"], G=c["G"], precision=lbm.FP32_SHIFTED)
+    g.init(rho0)
+    g.step(10)
+    g.init(rho0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.step(c["steps"])
+    t_fwd = time.perf_counter() - t0
+    target = g.fields(u=False, p=False, psi=False)["rho"]
+    g.close()
+    spec = dict(shape=shape, components=comps, T=c["T"], tau=c["tau"], gamma=c["gamma"], beta=c["beta"], G=c["G"],
+                steps=c["steps"], checkpoint_every=c["checkpoint_every"], rho0=rho0, precision=lbm.FP32_SHIFTED,
+                pair=(0, 1), least_volatile=int(c["least_volatile"]))
+    zeta = torch.tensor(0.0, dtype=torch.float64, requires_grad=True)
+    s = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    t0 = time.perf_counter()
+    rho = LatticeRun.apply(zeta, s, spec)
+    t_rec = time.perf_counter() - t0
+    L = composition_profile_loss(rho, torch.from_numpy(target), [d["M"] for d in c["components"]])
+    t0 = time.perf_counter()
+    L.backward()
+    t_back = time.perf_counter() - t0
+    out = {"steps": c["steps"], "checkpoint_every": c["checkpoint_every"], "forward_s": t_fwd,
+           "recorded_forward_s": t_rec, "backward_s": t_back, "cost_vs_forward": (t_rec + t_back) / t_fwd,
+           "target": 3.0, "loss": float(L), "dL_dk12": zeta.grad.item(), "dL_ds": s.grad.item(),
+           "timing": "host clock around lbm_step / LatticeRun.apply / loss.backward (each synchronises)"}
+    if "loss_dk12" in ref:
+        out["oracle"] = {"loss": float(ref["loss_value"]), "dL_dk12": float(ref["loss_dk12"]),
+                         "dL_ds": float(ref["loss_ds"])}
+        out["rel_err"] = {"dL_dk12": abs(zeta.grad.item() / float(ref["loss_dk12"]) - 1),
+                          "dL_ds": abs(s.grad.item() / float(ref["loss_ds"]) - 1)}
+    return out
+
+
+def cpu_baselines(budget_s=2.5):
+    """The oracle as it stands on the host cores for each workload, on one core and on all of
+    them: a bounded sample of each (stated), steps timed until about budget_s per setting."""
+    import lbm_inputs
+    import oracle
+    cores = oracle.threads()
+    out = {}
+
+    def timed(case, f):
+        f = oracle.step(case, f, 1)
+        n, t0 = 0, time.perf_counter()
+        while True:
+            f = oracle.step(case, f, 1)
+            n += 1
+            el = time.perf_counter() - t0
+            if el > budget_s:
+                return case.nsites * case.nc * n / el / 1e6, n
+
+    def case_of(c, shape, Q):
+        k = [(d["Tc"], d["pc"], d["omega"], d["M"]) for d in c["components"]]
+        coll = 1 if c.get("collision") == "mrt" else 0
+        return oracle.Case(Q=Q, shape=tuple(shape), Tc=[x[0] for x in k], pc=[x[1] for x in k],
+                           omega=[x[2] for x in k], M=[x[3] for x in k], T=c["T"], tau=c["tau"], gamma=c["gamma"],
+                           kij=c["kij"], beta=c["beta"], G=c["G"], collision=coll,
+                           s=c.get("mrt_s") if coll else None)
+
+    samples = []
+    c1 = load_case("c1")
+    samples.append(("c1_slab", c1, c1["shape"], 9, case_fields(c1), "the full 64^2 FP64 BGK slab"))
+    c2 = load_case("c2")
+    r2 = c2["init"]["radius"] / 4
+    g2 = (128, 128)
+    samples.append(("c2_droplet", c2, [128, 128], 9,
+                    lbm_inputs.ball_fields(g2, c2["rho_l"], c2["rho_v"], r2, 4.0),
+                    "128^2 box of the MRT droplet (radius scaled by 1/4)"))
+    c3 = load_case("c3")
+    samples.append(("c3_sphere", c3, [32, 32, 32], 19,
+                    lbm_inputs.ball_fields((32, 32, 32), c3["rho_l"], c3["rho_v"], 6.0, 4.0),
+                    "32^3 box of the MRT sphere (radius scaled by 1/8)"))
+    with open(os.path.join(ROOT, "tests", "golden", "cases.json")) as fh:
+        sw = json.load(fh)["c4"]
+    specs, rhos = _sweep_specs(sw)
+    c4 = dict(sw["cases"][0], tau=sw["tau"], beta=sw["beta"], collision="bgk")
+    samples.append(("c4_sweep", c4, c4["shape"], 9, rhos[0], "sweep case 0 (%dx%d, BGK)" % tuple(c4["shape"])))
+    c5 = load_case("c5")
+    samples.append(("c5_adjoint_droplet", c5, c5["shape"], 9, init_fields_ball(c5, tuple(reversed(c5["shape"]))),
+                    "the full 256^2 BGK droplet (forward step)"))
+    for name, c, shape, Q, rho, what in samples:
+        case = case_of(c, shape, Q)
+        f = oracle.equilibrium(case, rho)
+        row = {"sample": what, "unit": UNIT}
+        for label, n in (("one_core", 1), ("all_cores", cores)):
+            oracle.set_threads(n)
+            v, steps = timed(case, f)
+            row[label] = {"value": v, "cores": n, "steps": steps}
+        out[name] = row
+    oracle.set_threads(cores)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -358,8 +573,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--path", default="auto", choices=["auto", "fused", "two"],
+    ap.add_argument("--path", default="auto", choices=["auto", "fused", "two", "trailing"],
                     help="step path of the timed run (default: the library's choice)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the per-workload error check against the stored oracle runs")
     ap.add_argument("--grid", type=int, default=0,
                     help="cube edge of a smaller case of the same workload (profiling); 0 = 256")
     ap.add_argument("--nz", type=int, default=0,
@@ -399,7 +616,7 @@ def main():
 
     gpu = lattice_for(c, lbm.FP32_SHIFTED)
     if args.path != "auto":
-        gpu.set_path(lbm.PATH_FUSED if args.path == "fused" else lbm.PATH_TWO_KERNEL)
+        gpu.set_path({"fused": lbm.PATH_FUSED, "two": lbm.PATH_TWO_KERNEL, "trailing": lbm.PATH_TRAILING}[args.path])
     gpu.init(rho0)
     gpu.step(args.warmup)
     start = torch.cuda.Event(enable_timing=True)
@@ -441,7 +658,12 @@ def main():
     # move exactly that; psi traffic is not counted)
     peak, peak_kind = peaks()
     alg_site = 2 * 19 * nc * 4
-    if path == lbm.PATH_FUSED:
+    if path == lbm.PATH_TRAILING:
+        kname, kavg = "k_trail3", fus_ms / max(fus_n, 1)
+        kinds = {kname: kavg}
+        if psi_n:
+            kinds["k_psi (first step of the call)"] = psi_ms / psi_n
+    elif path == lbm.PATH_FUSED:
         kname = "k_fused3" if gpu.fused_kind == lbm.FUSED_PLANES else "k_fused"
         kavg = fus_ms / max(fus_n, 1)
         kinds = {kname: kavg}
@@ -454,7 +676,7 @@ def main():
             "kernel": "%s<19,%d,FP32S,MRT>" % (kname, nc), "peak_kind": peak_kind,
             "alg_bytes_per_launch": N * alg_site,
             "step_frac": (N * alg_site / (ms_step / 1e3) / 1e9) / peak,
-            "kernels_ms_avg": kinds, "path": "fused" if path == lbm.PATH_FUSED else "two-kernel"}
+            "kernels_ms_avg": kinds, "path": PATH_NAMES[path]}
 
     # end to end through the C ABI with pinned host buffers: the densities go in, the steps
     # run, the densities come back
@@ -494,14 +716,16 @@ def main():
         variants["fp64"] = {"value": N * nc / (ms64 / 1e3) / 1e6, "ms_per_step": ms64,
                             "hbm_frac_of_step": (N * 2 * 19 * nc * 8 / (ms64 / 1e3) / 1e9) / peak}
         variants["fp32s"] = {"value": value, "ms_per_step": ms_step, "path": roof["path"]}
-        # the same workload on the other step path
-        other = lbm.PATH_FUSED if path == lbm.PATH_TWO_KERNEL else lbm.PATH_TWO_KERNEL
-        g2 = lattice_for(c, lbm.FP32_SHIFTED)
-        try:
-            g2.set_path(other)
-        except lbm.LBMError:
-            other = None
-        if other is not None:
+        # the same workload on the other step paths
+        for other in (lbm.PATH_TWO_KERNEL, lbm.PATH_TRAILING, lbm.PATH_FUSED):
+            if other == path:
+                continue
+            g2 = lattice_for(c, lbm.FP32_SHIFTED)
+            try:
+                g2.set_path(other)
+            except lbm.LBMError:
+                g2.close()
+                continue
             g2.init(rho0)
             g2.step(3)
             g2.set_stream(stream.cuda_stream)
@@ -510,17 +734,18 @@ def main():
             b.record(stream)
             torch.cuda.synchronize()
             ms2 = a.elapsed_time(b) / 50
-            name = "fp32s_fused" if other == lbm.PATH_FUSED else "fp32s_two_kernel"
-            variants[name] = {"value": N * nc / (ms2 / 1e3) / 1e6, "ms_per_step": ms2,
-                              "hbm_frac_of_step": (N * alg_site / (ms2 / 1e3) / 1e9) / peak}
-        g2.close()
+            variants["fp32s_" + PATH_NAMES[other].replace("-", "_")] = {
+                "value": N * nc / (ms2 / 1e3) / 1e6, "ms_per_step": ms2,
+                "hbm_frac_of_step": (N * alg_site / (ms2 / 1e3) / 1e9) / peak}
+            g2.close()
         variants["batched"] = batched_variant(stream)
         variants["l2_resident"] = l2_variants(stream)
         variants["flash"] = flash_variant()
+        variants["adjoint"] = adjoint_variant()
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "eos_dtype": "f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": "f32", "precision": EOS_PRECISION, "data": "synthetic",
            "config": {"workload": WORKLOAD, "lattice": "D3Q19", "grid": c["shape"], "components": nc,
                       "collision": "mrt", "precision": "fp32-shifted", "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs larger than L2 (%.2f GB populations)" % (N * 19 * nc * 4 / 1e9)},
@@ -533,9 +758,12 @@ def main():
            "mass_drift": float(np.max(np.abs(mass_end / (rho0.reshape(nc, -1).sum(1)) - 1)))}
     if variants:
         out["variants"] = variants
+    if rank == 0 and not args.no_configs:
+        out["configs_vs_oracle"] = config_checks()
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"], sample = cpu_baseline(c)
         out["err_vs_oracle"] = accuracy(c, sample)
+        out["cpu_baselines"] = cpu_baselines()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

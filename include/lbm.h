@@ -123,9 +123,14 @@ lbm_status lbm_set_stream(lbm_ctx *ctx, void *stream);
  * returns after the last read either way. */
 lbm_status lbm_init(lbm_ctx *ctx, const double *rho, const double *u);
 
-/* Advances n >= 0 steps. On a failing step the kernels of the remaining steps do nothing,
- * the populations hold the state before the failing step (two-kernel path) and the status
- * of the failure is returned; lbm_time then gives the index of that step. */
+/* Advances n >= 0 steps of Section 3.4's implementation list: per step the cell-volume
+ * densities (moments of Eq. LBE), the mixture Peng-Robinson pressure (Eq. MCPengRobinson with
+ * Eq. randommixingrule), the pseudo-potential (Eq. psicorrected), the total force (Eq.
+ * coupledMCforce), its split (Eq. distributionforce, or Eq. Gong) and the forced collision and
+ * streaming of every component (Eq. LBE, Eq. equilibrium a, b). On a failing step the kernels
+ * of the remaining steps do nothing, the populations hold the state before the failing step
+ * and the status of the failure is returned; lbm_time then gives the index of that step (on
+ * LBM_PATH_FUSED after a timeout the state is undefined). */
 lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
 
 /* Number of steps taken since the last lbm_init / lbm_set_f. */
@@ -138,18 +143,21 @@ int64_t lbm_time(const lbm_ctx *ctx);
  * call returns after the last write either way. */
 lbm_status lbm_fields(lbm_ctx *ctx, double *rho, double *u, double *p, double *psi);
 
-/* Total mass of each component, sum over sites of rho_s (the step's S7 reduction), into host
- * mass[nc]. FP32-shifted storage: each thread sums its populations with a compensated FP32
+/* Total mass of each component, sum over sites of rho_s, into host mass[nc]: the quantity
+ * Eq. LBE conserves for every component (the collision and the Guo force term of Eq.
+ * equilibrium b have no zeroth moment, streaming permutes the populations). FP32-shifted storage: each thread sums its populations with a compensated FP32
  * sum (TwoSum, about 2^-48 relative) and the reference shift N rho_ref_s is added once; FP64
  * storage sums in FP64. The grid and every reduction are fixed, so the result is
  * bit-reproducible on a given device. Synchronous: returns after the copy to host. */
 lbm_status lbm_mass(lbm_ctx *ctx, double *mass);
 
-/* Current populations in the canonical FP64 layout f[nc][Q][N] (shift added back). */
+/* Current populations f_{s,a}(x) of Eq. LBE (the distribution functions of every component
+ * and direction) in the canonical FP64 layout f[nc][Q][N] (shift added back). */
 lbm_status lbm_get_f(lbm_ctx *ctx, double *f);
 
-/* Replaces the populations with host f[nc][Q][N] (canonical FP64 layout; rounded to FP32
- * after subtracting the shift when the context stores FP32) and sets the step counter to 0. */
+/* Replaces the populations f_{s,a}(x) of Eq. LBE with host f[nc][Q][N] (canonical FP64 layout;
+ * rounded to FP32 after subtracting the shift when the context stores FP32) and sets the step
+ * counter to 0. */
 lbm_status lbm_set_f(lbm_ctx *ctx, const double *f);
 
 /* Size in bytes of the raw population storage (lbm_save / lbm_restore). */
@@ -178,18 +186,29 @@ lbm_status lbm_restore(lbm_ctx *ctx, const void *buf, size_t bytes, int64_t t);
  * faster one on GB300 for both lattices. Setting LBM_PATH_FUSED on a grid it does not fit returns LBM_ERR_ARG and leaves the
  * two-kernel path. All paths compute the same arithmetic in the same order per site, so their
  * results are bit-identical. */
-enum { LBM_PATH_AUTO = 0, LBM_PATH_TWO_KERNEL = 1, LBM_PATH_FUSED = 2 };
+/* LBM_PATH_TRAILING (D3Q19, nz >= 3): one persistent cooperative kernel per step, one CTA per
+ * SM, CTA b owning a contiguous range of every z plane and marching z. psi of the step was
+ * computed by the previous step (a pseudo-potential pass precedes the first step of an
+ * lbm_step call when the state changed in between), so the collisions wait for nothing; a
+ * stage a few planes behind the collision computes psi of the NEXT step from the populations
+ * just written (re-read from L2), once the CTAs owning neighbour sites have published
+ * (release flags, bounded acquire waits) that they collided the planes around it. The
+ * populations are read from DRAM once per step and written once; psi of the next step is
+ * written to a second psi field. A failing psi (EOS domain, non-finite) ends the step that
+ * computed it normally and is reported for the next step, whose index lbm_time then gives,
+ * with the populations of the state before it, as on the other paths. */
+enum { LBM_PATH_AUTO = 0, LBM_PATH_TWO_KERNEL = 1, LBM_PATH_FUSED = 2, LBM_PATH_TRAILING = 3 };
 lbm_status lbm_set_path(lbm_ctx *ctx, int path);
-/* The path lbm_step takes now (LBM_PATH_TWO_KERNEL or LBM_PATH_FUSED). */
+/* The path lbm_step takes now (LBM_PATH_TWO_KERNEL, LBM_PATH_FUSED or LBM_PATH_TRAILING). */
 int lbm_get_path(const lbm_ctx *ctx);
-/* The form of the fused path: LBM_FUSED_TILES or LBM_FUSED_PLANES; 0 on the two-kernel path
- * or for a NULL ctx. */
+/* The form of the fused path: LBM_FUSED_TILES or LBM_FUSED_PLANES; 0 on the other paths or
+ * for a NULL ctx. */
 enum { LBM_FUSED_TILES = 1, LBM_FUSED_PLANES = 3 };
 int lbm_get_fused_kind(const lbm_ctx *ctx);
 
-/* Failure-detection test hook, fused path only: from the next step on, fused block `block`
- * (0-based; LBM_FUSED_TILES: x-tile fastest, then y-tile, then chunk; LBM_FUSED_PLANES: the
- * plane range index) computes but never publishes its
+/* Failure-detection test hook, fused and trailing paths only: from the next step on, fused
+ * block `block` (0-based; LBM_FUSED_TILES: x-tile fastest, then y-tile, then chunk;
+ * LBM_FUSED_PLANES and LBM_PATH_TRAILING: the plane range index) computes but never publishes its
  * progress, so every neighbour's bounded wait runs out and lbm_step returns
  * LBM_ERR_TIMEOUT (within about a second per step, without faulting or hanging the GPU); the
  * populations are then undefined. -1 switches the hook off; lbm_init restores a state. */

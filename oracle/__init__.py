@@ -9,7 +9,11 @@ It shares no code with the CUDA library (paper_1909_12390_gb300) and imports not
 Parity status: every function here is pinned by a test against a value the paper prints, a
 closed form, an invariant or brute force (see tests/test_oracle_*.py). The MRT collision is
 not in the paper; it is pinned by its reduction to BGK when every rate equals 1/tau, by exact
-mass conservation and by the orthogonality of its moment basis.
+mass conservation and by the orthogonality of its moment basis. The forward-mode derivative
+(step_dual) is pinned by central differences of step, by the independence of its two
+directions and by the zero split derivative of the total density of identical components
+(tests/test_oracle_dual.py), which also pins both split factors through the component
+momenta a step produces.
 """
 from __future__ import annotations
 
@@ -67,6 +71,8 @@ def lib():
         _lib.oracle_lattice.argtypes = [ctypes.c_int, ip, dp]
         _lib.oracle_mrt_matrix.argtypes = [ctypes.c_int, dp, dp]
         _lib.oracle_threads.argtypes = []
+        _lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        _lib.oracle_set_threads.restype = None
     return _lib
 
 
@@ -244,6 +250,11 @@ def mrt_matrix(Q: int):
 def threads() -> int:
     """OpenMP threads the oracle's loops use (set OMP_NUM_THREADS before the first call)."""
     return int(lib().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's later loops (results do not depend on it)."""
+    lib().oracle_set_threads(int(n))
 
 
 def mass(f: np.ndarray) -> np.ndarray:

@@ -604,6 +604,12 @@ int oracle_equilibrium(const oracle_case* c, const double* rho, const double* u,
 // Threads the oracle's loops use (OpenMP; results do not depend on it).
 int oracle_threads(void) { return omp_get_max_threads(); }
 
+// Sets the threads of the oracle's later loops (the timed baseline runs it on one core and on
+// all of them); n < 1 is ignored.
+void oracle_set_threads(int n) {
+  if (n >= 1) omp_set_num_threads(n);
+}
+
 // Lattice tables, exported for the tests' invariants (velocity e [19][3], weights [19]).
 int oracle_lattice(int Q, int* e, double* w) {
   if (Q != 9 && Q != 19) return ORACLE_ERR_ARG;

@@ -69,6 +69,9 @@ struct lbm_ctx {
   // step path: the fused kernel when its tiling fits the grid and its blocks are co-resident
   int path_request = LBM_PATH_AUTO;
   bool fused = false;
+  // trailing step: the step whose psi fargs.psi_ring[t & 1] holds, -1 when stale (any change of
+  // the state other than a trailing step makes it stale)
+  int64_t trail_t = -1;
   lbm::FusedArgs fargs{};
   cudaError_t launch_err = cudaSuccess;
   // per-kernel event timing (lbm_profile): events recorded around every launch on the stream
@@ -262,8 +265,9 @@ void launch_steps(lbm_ctx* c, int64_t n, int64_t t0) {
         e1 = next_event(c);
       }
       if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], c->stream);
-      cudaError_t e = c->fargs.mode == 3 ? c->ops->fused3(c->P, c->f, c->status, c->t_dev, c->fargs, c->stream)
-                                         : c->ops->fused(c->P, c->f, c->psi, c->status, c->t_dev, c->fargs, c->stream);
+      cudaError_t e = c->fargs.mode == 4 ? c->ops->trail3(c->P, c->f, c->status, c->t_dev, c->fargs, c->stream)
+                      : c->fargs.mode == 3 ? c->ops->fused3(c->P, c->f, c->status, c->t_dev, c->fargs, c->stream)
+                                           : c->ops->fused(c->P, c->f, c->psi, c->status, c->t_dev, c->fargs, c->stream);
       if (e != cudaSuccess && c->launch_err == cudaSuccess) c->launch_err = e;
       if (e1 >= 0) {
         cudaEventRecord(c->ev_pool[e1], c->stream);
@@ -302,11 +306,12 @@ void free_fused(lbm_ctx* c) {
   cudaFree(c->fargs.psi_ring);
   c->fargs = lbm::FusedArgs{};
   c->fused = false;
+  c->trail_t = -1;
 }
 
 // Workers (plane ranges) of the plane-range kernel, or blocks of the tile-column kernel.
 int fused_blocks(const lbm_ctx* c) {
-  return c->fargs.mode == 3 ? c->fargs.G : c->fargs.ntx * c->fargs.nty * c->fargs.nchunk;
+  return c->fargs.mode >= 3 ? c->fargs.G : c->fargs.ntx * c->fargs.nty * c->fargs.nchunk;
 }
 // Progress counters of the active fused kernel.
 int fused_flags(const lbm_ctx* c) {
@@ -397,6 +402,70 @@ bool setup_fused3(lbm_ctx* c) {
 // Chooses the fused tiling: tiles of fused_tx x fused_ty sites across the grid, the slowest
 // axis cut into the largest number of chunks (each at least two groups of fused_group planes)
 // whose blocks are still all co-resident. Returns false when the grid does not tile or the blocks would not fit.
+// The trailing fused step (k_trail3, D3Q19): one CTA per SM (kT3Threads threads), CTA b
+// owning sites [b nxy / G, (b + 1) nxy / G) of every z plane, the neighbour CTAs of each CTA
+// (owners of the 8 in-plane neighbours of its sites) listed for its waits, and two psi fields.
+// Returns false when the grid is too small, a CTA would have more than kF3MaxNbr neighbours or
+// the device cannot hold the CTAs at once.
+bool setup_trail3(lbm_ctx* c) {
+  free_fused(c);
+  if (c->Q != 19 || !c->ops->trail3_max_blocks) return false;
+  const int nx = c->P.nx, ny = c->P.ny, nz = c->P.nz;
+  const long long nxy = (long long)nx * ny;
+  if (nz < 3 || nxy < 64) return false;
+  const int cap = c->ops->trail3_max_blocks();
+  if (cap <= 0) return false;
+  const int G = (int)std::min<long long>(cap, nxy / 32);
+  if (G < 2) return false;
+  std::vector<int> range(G + 1), owner(nxy), nbr((size_t)G * lbm::kF3MaxNbr, -1);
+  for (int b = 0; b <= G; ++b) range[b] = (int)((long long)b * nxy / G);
+  for (int b = 0; b < G; ++b)
+    for (int i = range[b]; i < range[b + 1]; ++i) owner[i] = b;
+  for (int b = 0; b < G; ++b) {
+    int n = 0;
+    for (int i = range[b]; i < range[b + 1]; ++i) {
+      const int x = i % nx, y = i / nx;
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int o = owner[(size_t)((y + dy + ny) % ny) * nx + (x + dx + nx) % nx];
+          if (o == b) continue;
+          bool seen = false;
+          for (int k = 0; k < n; ++k) seen = seen || nbr[(size_t)b * lbm::kF3MaxNbr + k] == o;
+          if (seen) continue;
+          if (n == lbm::kF3MaxNbr) return false;
+          nbr[(size_t)b * lbm::kF3MaxNbr + n++] = o;
+        }
+    }
+  }
+  lbm::FusedArgs a{};
+  a.mode = 4;
+  a.G = G;
+  a.smax = (int)((nxy + G - 1) / G);
+  a.silent_block = -1;
+  int* d_range = nullptr;
+  int* d_nbr = nullptr;
+  bool ok = cudaMalloc(&a.flags, (size_t)G * sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMalloc(&a.done, sizeof(unsigned int)) == cudaSuccess && cudaMalloc(&a.pending, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&d_range, (G + 1) * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&d_nbr, nbr.size() * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&a.psi_ring, (size_t)2 * c->P.N * c->ops->psi_bytes) == cudaSuccess;
+  a.range = d_range;
+  a.nbr = d_nbr;
+  ok = ok && cudaMemset(a.flags, 0, (size_t)G * sizeof(unsigned long long)) == cudaSuccess &&
+       cudaMemset(a.done, 0, sizeof(unsigned int)) == cudaSuccess && cudaMemset(a.pending, 0, sizeof(int)) == cudaSuccess &&
+       cudaMemcpy(d_range, range.data(), (G + 1) * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+  c->fargs = a;
+  if (!ok) {
+    cudaGetLastError();
+    free_fused(c);
+    return false;
+  }
+  c->fused = true;
+  c->trail_t = -1;
+  return true;
+}
+
 bool setup_fused(lbm_ctx* c) {
   free_fused(c);
   if (setup_fused3(c)) return true;
@@ -734,6 +803,7 @@ lbm_status lbm_init(lbm_ctx* c, const double* rho, const double* u) {
   CK(c, reset_fused_flags(c));
   CK(c, cudaStreamSynchronize(c->stream));
   c->t = 0;
+  c->trail_t = -1;
   return LBM_OK;
 }
 
@@ -741,6 +811,19 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n) {
   if (!c) return LBM_ERR_ARG;
   if (n < 0) return fail(c, LBM_ERR_ARG, "n must be >= 0");
   int64_t t = c->t, left = n;
+  const bool trailing = c->fused && c->fargs.mode == 4;
+  if (trailing && n > 0 && c->trail_t != t) {
+    // psi of the first step, which the trailing step reads from psi_ring[t & 1]
+    const int e0 = c->profiling ? next_event(c) : -1, e1 = c->profiling ? next_event(c) : -1;
+    if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], c->stream);
+    c->ops->psi(c->P, c->f, (char*)c->fargs.psi_ring + (size_t)(t & 1) * c->P.N * c->ops->psi_bytes, c->status,
+                (int)(t & 1), c->stream);
+    if (e1 >= 0) {
+      cudaEventRecord(c->ev_pool[e1], c->stream);
+      c->ev_marks[0].push_back({e0, e1});
+    }
+  }
+  if (!trailing) c->trail_t = -1;
   if ((t & 1) && left > 0) {  // reach an even step before replaying graphs
     launch_steps(c, 1, t);
     ++t;
@@ -752,6 +835,7 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n) {
     left -= kGraphSteps;
   }
   launch_steps(c, left, t);
+  c->trail_t = -1;
   if (c->launch_err != cudaSuccess) {
     cudaError_t e = c->launch_err;
     c->launch_err = cudaSuccess;
@@ -759,12 +843,14 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n) {
     return cuda_fail(c, e, "fused step launch");
   }
   CK(c, cudaGetLastError());
-  return sync_status(c);
+  lbm_status st = sync_status(c);
+  if (st == LBM_OK && trailing) c->trail_t = c->t;
+  return st;
 }
 
 lbm_status lbm_set_path(lbm_ctx* c, int path) {
   if (!c) return LBM_ERR_ARG;
-  if (path != LBM_PATH_AUTO && path != LBM_PATH_TWO_KERNEL && path != LBM_PATH_FUSED)
+  if (path != LBM_PATH_AUTO && path != LBM_PATH_TWO_KERNEL && path != LBM_PATH_FUSED && path != LBM_PATH_TRAILING)
     return fail(c, LBM_ERR_ARG, "unknown path %d", path);
   CK(c, cudaStreamSynchronize(c->stream));
   drop_graph(c);
@@ -776,6 +862,11 @@ lbm_status lbm_set_path(lbm_ctx* c, int path) {
   }
   if (path == LBM_PATH_AUTO) {
     setup_auto(c);
+    return LBM_OK;
+  }
+  if (path == LBM_PATH_TRAILING) {
+    if (!setup_trail3(c))
+      return fail(c, LBM_ERR_ARG, "the trailing step needs D3Q19, nz >= 3 and co-resident CTAs for this grid");
     return LBM_OK;
   }
   if (!setup_fused(c))
@@ -795,10 +886,14 @@ lbm_status lbm_test_silence_block(lbm_ctx* c, int block) {
   return LBM_OK;
 }
 
-int lbm_get_path(const lbm_ctx* c) { return c ? (c->fused ? LBM_PATH_FUSED : LBM_PATH_TWO_KERNEL) : -1; }
+int lbm_get_path(const lbm_ctx* c) {
+  if (!c) return -1;
+  if (!c->fused) return LBM_PATH_TWO_KERNEL;
+  return c->fargs.mode == 4 ? LBM_PATH_TRAILING : LBM_PATH_FUSED;
+}
 
 int lbm_get_fused_kind(const lbm_ctx* c) {
-  if (!c || !c->fused) return 0;
+  if (!c || !c->fused || c->fargs.mode == 4) return 0;
   return c->fargs.mode == 3 ? LBM_FUSED_PLANES : LBM_FUSED_TILES;
 }
 
@@ -899,6 +994,7 @@ lbm_status lbm_set_f(lbm_ctx* c, const double* f) {
   if (e == cudaSuccess) e = cudaMemsetAsync(c->t_dev, 0, sizeof(long long), c->stream);
   if (e == cudaSuccess) e = reset_fused_flags(c);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  c->trail_t = -1;
   if (e != cudaSuccess) return cuda_fail(c, e, "lbm_set_f");
   c->t = 0;
   return LBM_OK;
@@ -924,6 +1020,7 @@ lbm_status lbm_restore(lbm_ctx* c, const void* buf, size_t bytes, int64_t t) {
   CK(c, cudaMemcpyAsync(c->f, buf, bytes, cudaMemcpyHostToDevice, c->stream));
   long long tt = t;
   CK(c, cudaMemcpyAsync(c->t_dev, &tt, sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+  c->trail_t = -1;
   CK(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
   CK(c, reset_fused_flags(c));
   CK(c, cudaStreamSynchronize(c->stream));
@@ -940,6 +1037,7 @@ lbm_status lbm_record(lbm_ctx* c, int64_t n, int checkpoint_every) {
   for (void* p : c->ckpt) cudaFree(p);
   c->ckpt.clear();
   c->rec_t0 = -1;
+  c->trail_t = -1;
   const size_t bytes = lbm_state_bytes(c);
   const int64_t t0 = c->t;
   for (int64_t done = 0; done < n;) {

@@ -55,15 +55,18 @@ constexpr int kCollideBlocks = LBM_COLLIDE_BLOCKS;
 #define LBM_COLLIDE_GROUP 9
 #endif
 
-// Population stores into global memory are marked evict-first (st.global.cs): the written
-// populations are not read again in the step, and keeping them out of the way leaves L2 to the
-// populations still to be read. GLOBAL = 0 selects a plain (generic) store, required when the
-// populations live in shared memory (the batched kernel): st.global on a shared address is an
-// address-space fault.
+// Population stores into global memory are marked evict-first (st.global.cs, GLOBAL = 1): the
+// written populations are not read again in the step, and keeping them out of the way leaves L2
+// to the populations still to be read. GLOBAL = 2 is a plain global store (st.global.wb), for a
+// step that re-reads what it wrote from L2. GLOBAL = 0 selects a generic store, required when
+// the populations live in shared memory (the batched kernel): st.global on a shared address is
+// an address-space fault.
 template <class Prec, int GLOBAL>
 __device__ __forceinline__ void store_pop(typename Prec::S* p, typename Prec::R v) {
-  if constexpr (GLOBAL)
+  if constexpr (GLOBAL == 1)
     __stcs(p, (typename Prec::S)v);
+  else if constexpr (GLOBAL == 2)
+    __stwb(p, (typename Prec::S)v);  // global memory, kept in L2 (write-back)
   else
     *p = (typename Prec::S)v;
 }
@@ -111,21 +114,56 @@ __device__ __forceinline__ int site_psi_dl(const Params& P, const typename Prec:
   return 0;
 }
 
-// Shifted densities of one site, summed in the same order as site_moments (rest, then the
-// pairs), so that every path computes bit-identical densities.
+// Order in which a site's populations are summed into its density, the same on every path:
+// grouped by the direction's component along the slowest axis (z in 3-D, y in 2-D),
+//   rho_s = (G_up + G_mid) + G_down,  G_up = sum over e_last = +1, G_mid over e_last = 0,
+//   G_down over e_last = -1, each group summed left to right in ascending direction index.
+// After a step f_a(x) = f*_a(x - e_a), so G_up of a site holds values collided on the plane
+// below it, G_mid on its own plane and G_down on the plane above: a step that marches the
+// slowest axis can form the next step's densities from the values it has just written, in
+// this same order (bit for bit what a separate pass over the stored values computes).
+template <int Q>
+struct DensOrder {
+  static constexpr int D = Lat<Q>::D;
+  __host__ __device__ static constexpr int grp(int a) { return Lat<Q>::e(a, D - 1); }
+  // k-th direction of group g (+1, 0, -1) in ascending index, -1 past its end
+  __host__ __device__ static constexpr int dir(int g, int k) {
+    for (int a = 0; a < Q; ++a)
+      if (grp(a) == g && k-- == 0) return a;
+    return -1;
+  }
+  __host__ __device__ static constexpr int count(int g) {
+    int n = 0;
+    for (int a = 0; a < Q; ++a) n += grp(a) == g ? 1 : 0;
+    return n;
+  }
+};
+
+// Sum of the populations of group g at site s, in the order above; V(a) returns f_a.
+template <int Q, int G, class R, class V>
+__device__ __forceinline__ R dens_group(V&& v) {
+  using DO = DensOrder<Q>;
+  R acc = v(std::integral_constant<int, DO::dir(G, 0)>{});
+  For<1, DO::count(G)>::run([&]<int K>() { acc += v(std::integral_constant<int, DO::dir(G, K)>{}); });
+  return acc;
+}
+template <int Q, class R, class V>
+__device__ __forceinline__ R dens_sum(V&& v) {
+  const R up = dens_group<Q, 1, R>(v);
+  const R mid = dens_group<Q, 0, R>(v);
+  const R down = dens_group<Q, -1, R>(v);
+  return (up + mid) + down;
+}
+
+// Shifted densities of one site, summed in the order of DensOrder (as site_moments does), so
+// that every path computes bit-identical densities.
 template <int Q, int NC, class Prec, int PAR>
 __device__ __forceinline__ void site_densities(const Params& P, const typename Prec::S* __restrict__ f,
                                                const Site& s, typename Prec::R (&d)[NC]) {
   using R = typename Prec::R;
-  using L = Lat<Q>;
   For<0, NC>::run([&]<int C>() {
     const typename Prec::S* fc = comp_base<Q>(f, P, C);
-    R acc = (R)fc[AA<Q>::template rd<0, PAR>(P, s)];
-    For<0, L::NPAIR>::run([&]<int K>() {
-      constexpr int a = L::pfirst(K), b = L::opp(a);
-      acc += (R)fc[AA<Q>::template rd<a, PAR>(P, s)] + (R)fc[AA<Q>::template rd<b, PAR>(P, s)];
-    });
-    d[C] = acc;
+    d[C] = dens_sum<Q, R>([&](auto a_) { return (R)fc[AA<Q>::template rd<decltype(a_)::value, PAR>(P, s)]; });
   });
 }
 
@@ -190,33 +228,50 @@ __device__ __forceinline__ void gong_split(const Params& P, const R (&rc)[NC], R
   for (int i = 0; i < NC; ++i) chi[i] = (R)(w[i] / ws);
 }
 
-// S1 moments of one site: shifted component densities dl_c = sum_a f_ca = rho_c - rho_ref_c
-// and the total momentum j = sum_c sum_a e_a f_ca. The momentum is summed from the differences
-// of opposite populations: near equilibrium the two are close, so in FP32 each difference is
-// exact and j carries no rounding on the scale of the populations.
+// S1 moments of one component c at one site: its shifted density dl_c = sum_a f_ca =
+// rho_c - rho_ref_c (in the order of DensOrder) and its momentum j_c = sum_a e_a f_ca, summed
+// from the differences of opposite populations: near equilibrium the two are close, so in FP32
+// each difference is exact and j carries no rounding on the scale of the populations.
+template <int Q, int C, class Prec, int PAR>
+__device__ __forceinline__ void comp_moments(const Params& P, const typename Prec::S* __restrict__ f, const Site& s,
+                                             typename Prec::R& dl, typename Prec::R (&jc)[3]) {
+  using R = typename Prec::R;
+  using L = Lat<Q>;
+  const typename Prec::S* fc = comp_base<Q>(f, P, C);
+  R v[Q];
+  For<0, Q>::run([&]<int A>() { v[A] = (R)fc[AA<Q>::template rd<A, PAR>(P, s)]; });
+  dl = dens_sum<Q, R>([&](auto a_) { return v[decltype(a_)::value]; });
+  jc[0] = jc[1] = jc[2] = 0;
+  For<0, L::NPAIR>::run([&]<int K>() {
+    constexpr int a = L::pfirst(K), b = L::opp(a);
+    const R d = v[a] - v[b];
+#pragma unroll
+    for (int k = 0; k < L::D; ++k) {
+      if (L::e(a, k) > 0) jc[k] += d;
+      if (L::e(a, k) < 0) jc[k] -= d;
+    }
+  });
+}
+
+// The site's total momentum from the components' momenta, summed in component order.
+template <int NC, class R>
+__device__ __forceinline__ void sum_momenta(const R (&jc)[NC][3], R (&j)[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    j[k] = jc[0][k];
+#pragma unroll
+    for (int c = 1; c < NC; ++c) j[k] += jc[c][k];
+  }
+}
+
+// S1 moments of one site: the shifted densities of every component and the total momentum.
 template <int Q, int NC, class Prec, int PAR>
 __device__ __forceinline__ void site_moments(const Params& P, const typename Prec::S* __restrict__ f, const Site& s,
                                              typename Prec::R (&dl)[NC], typename Prec::R (&j)[3]) {
   using R = typename Prec::R;
-  using L = Lat<Q>;
-  j[0] = j[1] = j[2] = 0;
-  For<0, NC>::run([&]<int C>() {
-    const typename Prec::S* fc = comp_base<Q>(f, P, C);
-    R acc = (R)fc[AA<Q>::template rd<0, PAR>(P, s)];
-    For<0, L::NPAIR>::run([&]<int K>() {
-      constexpr int a = L::pfirst(K), b = L::opp(a);
-      const R va = (R)fc[AA<Q>::template rd<a, PAR>(P, s)];
-      const R vb = (R)fc[AA<Q>::template rd<b, PAR>(P, s)];
-      acc += va + vb;
-      const R d = va - vb;
-#pragma unroll
-      for (int k = 0; k < L::D; ++k) {
-        if (L::e(a, k) > 0) j[k] += d;
-        if (L::e(a, k) < 0) j[k] -= d;
-      }
-    });
-    dl[C] = acc;
-  });
+  R jc[NC][3];
+  For<0, NC>::run([&]<int C>() { comp_moments<Q, C, Prec, PAR>(P, f, s, dl[C], jc[C]); });
+  sum_momenta<NC, R>(jc, j);
 }
 
 // The two members of a pair of opposite populations pass through identical arithmetic. In
@@ -264,25 +319,31 @@ __device__ __forceinline__ V2<double> fma2(V2<double> a, V2<double> b, V2<double
 __device__ __forceinline__ V2<double> add2(V2<double> a, V2<double> b) { return {a.x + b.x, a.y + b.y}; }
 __device__ __forceinline__ V2<double> mul2(V2<double> a, V2<double> b) { return {a.x * b.x, a.y * b.y}; }
 
-// S4-S6 of one site given psi at the site (pn[0]) and its Q - 1 neighbours (pn[a] at x + e_a)
-// and the site's moments: total force, split, Guo-forced BGK or MRT collision, in-place AA
-// write. Everything is arranged over the pairs of opposite directions (a, b = opp(a)):
-//   * the equilibrium is w_a (dl_c + rho_c P_a) with P_a = Pe +- Po (even / odd parts of
-//     3 e.u + 9/2 (e.u)^2 - 3/2 u.u); its large even part w (dl_c + rho_c Pe) is the same for
-//     both members and is subtracted from each population inside a multiply-add, never
-//     rounded on its own;
-//   * the Guo term Fb_a = w_a [3 (e_a - u).F + 9 (e_a.u)(e_a.F)] = Fe +- Fo likewise;
-//   * the MRT correction acts on the free rows through pair sums (even rows, one coefficient
-//     per pair class) and pair differences (odd rows);
-//   * the change d_a of each population is formed in full before it is added to the stored
-//     value, so the population is rounded once.
-// In FP32 these keep the rounding of the large quantities out of the momentum balance; a
-// textbook per-direction evaluation lets that rounding drive a random walk of the total
-// momentum, and long runs of a liquid slab then drift measurably.
-template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1, int PT = LBM_COLLIDE_PAIRS>
-__device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S* __restrict__ f, const Site& s,
-                                               const typename Prec::R (&pn)[Q], const typename Prec::R (&dl)[NC],
-                                               const typename Prec::R (&j)[3], typename Prec::S* fo = nullptr) {
+// Per-site values shared by every component's collision (S4, S5 and the velocity of
+// Eq. equilibrium), computed once per site by site_prep and read by comp_collide.
+template <int Q, int NC, class R, int PT>
+struct SitePrep {
+  R rc[NC], dl[NC], chis[NC];
+  R u[3], F[3], uF, P0, F0;
+  R pt_r[PT ? 4 * Lat<Q>::NPAIR : 1];
+};
+
+// e_a . v for a compile-time direction a (additions only).
+template <int Q, int A, class R>
+__device__ __forceinline__ R edot(const R (&v)[3]) {
+  R x = 0;
+#pragma unroll
+  for (int d = 0; d < Lat<Q>::D; ++d) {
+    if (Lat<Q>::e(A, d) > 0) x += v[d];
+    if (Lat<Q>::e(A, d) < 0) x -= v[d];
+  }
+  return x;
+}
+
+template <int Q, int NC, class Prec, int PT = LBM_COLLIDE_PAIRS>
+__device__ __forceinline__ void site_prep(const Params& P, const typename Prec::R (&pn)[Q],
+                                          const typename Prec::R (&dl)[NC], const typename Prec::R (&j)[3],
+                                          SitePrep<Q, NC, typename Prec::R, PT>& sp) {
   using R = typename Prec::R;
   using L = Lat<Q>;
   constexpr int D = L::D;
@@ -312,11 +373,13 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
     }
   });
   const R k1p = PC<R>::k1(P) * pn[0], k2 = PC<R>::k2(P);
-  R F[3] = {0, 0, 0};
+  R* F = sp.F;
+  F[0] = F[1] = F[2] = 0;
 #pragma unroll
   for (int d = 0; d < D; ++d) F[d] = fmx(k1p, S1[d], k2 * S2[d]);
 
-  R rc[NC], rho = 0, gs = 0;
+  R (&rc)[NC] = sp.rc;
+  R rho = 0, gs = 0;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     rc[c] = PC<R>::rho_ref(P, c) + dl[c];
@@ -324,7 +387,8 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
     gs = fmx(PC<R>::gamma(P, c), rc[c], gs);
   }
   // barycentric velocity with the Guo half force
-  R u[3] = {0, 0, 0};
+  R* u = sp.u;
+  u[0] = u[1] = u[2] = 0;
   const R irho = (R)1 / rho;
 #pragma unroll
   for (int d = 0; d < D; ++d) u[d] = fmx((R)0.5, F[d], j[d]) * irho;
@@ -334,40 +398,30 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
     uu = fmx(u[d], u[d], uu);
     uF = fmx(u[d], F[d], uF);
   }
+  sp.uF = uF;
   // Per pair p the even / odd parts of P_a = 3 e.u + 9/2 (e.u)^2 - 3/2 u.u (Pe +- Po) and of
   // Fb_a = w_a [3 (e_a - u).F + 9 (e_a.u)(e_a.F)] (Fe +- Fo) are formed inside each
   // component's loop from e_p.u and e_p.F (a few adds; keeping them per site would hold
   // 2 (Q - 1) more registers through the component loop).
-  auto dot = [&](const R (&v)[3], auto a_) {
-    constexpr int a = decltype(a_)::value;
-    R x = 0;
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      if (L::e(a, d) > 0) x += v[d];
-      if (L::e(a, d) < 0) x -= v[d];
-    }
-    return x;
-  };
   const R P0 = -(R)1.5 * uu;
   const R F0 = -(R)(3.0 * L::w(0)) * uF;
+  sp.P0 = P0;
+  sp.F0 = F0;
   // per-pair values of the site (PT = 1): [0] Pe, [1] e.u, [2] Fe, [3] Fo
-  R pt_r[PT ? 4 * NP : 1];
-  auto pt = [&](int i, int k) -> R& { return pt_r[PT ? i * NP + k : 0]; };
+  auto pt = [&](int i, int k) -> R& { return sp.pt_r[PT ? i * NP + k : 0]; };
   if constexpr (PT) {
     For<0, NP>::run([&]<int K>() {
       constexpr int a = L::pfirst(K);
-      const R eu = dot(u, std::integral_constant<int, a>{});
-      const R eF = dot(F, std::integral_constant<int, a>{});
+      const R eu = edot<Q, a>(sp.u);
+      const R eF = edot<Q, a>(sp.F);
       pt(0, K) = fmx((R)4.5 * eu, eu, P0);
       pt(1, K) = eu;
       pt(2, K) = (R)L::w(a) * fmx((R)9 * eu, eF, (R)-3 * uF);
       pt(3, K) = (R)(3.0 * L::w(a)) * eF;
     });
   }
-  const R om = PC<R>::omega(P);
-  const R gk = PC<R>::gk(P);
   // S5: split factors
-  R chis[NC];
+  R (&chis)[NC] = sp.chis;
   if (P.split == 0) {
     const R igs = (R)1 / gs;
 #pragma unroll
@@ -375,186 +429,230 @@ __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S
   } else {
     gong_split<NC, R>(P, rc, chis);
   }
-  For<0, NC>::run([&]<int C>() {
-    // Compiler-only barrier: the populations are re-read (from L1) rather than kept in
-    // registers from the moments pass, which would cost Q * NC registers.
-    asm volatile("" ::: "memory");
-    const R chi = chis[C];
-    const R gkchi = gk * chi;
-    typename Prec::S* fc = comp_base<Q>(f, P, C);
-    // the new values go to the same slots of fo when given (a step out of place: each site
-    // writes exactly the slots it reads), else in place
-    typename Prec::S* fcw = comp_base<Q>(fo ? fo : f, P, C);
-    // Non-equilibrium part g = f - f_eq (stored variables) per pair: A is the even part of the
-    // equilibrium (one value for both members), B the odd part; the BGK + Guo change is
-    // d = gk chi Fb - omega g. For MRT a first pass accumulates the free-row moments of
-    // q = g + chi Fb / 2 in pair form (q_a + q_b = g_a + g_b + chi Fe, q_a - q_b =
-    // g_a - g_b + chi Fo; even rows through per-class sums, odd rows directly); the second
-    // pass re-reads the populations (L1), forms d and the MRT correction and stores. Keeping
-    // nothing per pair between the passes keeps the register count down.
-    // Per-pair values are the same for every component and both passes. With PT = 1 they
-    // come from the table computed once per site (4 registers per pair: about 9 instructions
-    // per pair and pass fewer, and fewer spills at 128 registers). With PT = 0 u, F and u.F
-    // pass through an empty asm, which makes them opaque per pass, so the values are
-    // recomputed from them (a few FMAs per pair) instead of held.
-    R uo[3], Fo_[3], uFo = uF, P0o = P0;
-    // The site's addresses are likewise made opaque per pass. Besides bounding the registers,
-    // this keeps the instruction stream of the collision the same in every kernel that
-    // inlines it: without it the fused and two-kernel steps were measured to differ in the
-    // last bit (the multiply-add contractions follow the instruction order).
-    Site so = s;
-    auto refresh = [&]() {
-      so = s;
-      opaque(so);
-      if constexpr (!PT) {  // with the table, u, F and u.F are not needed after it is filled
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          uo[d] = u[d];
-          Fo_[d] = F[d];
-          opaque(uo[d]);
-          opaque(Fo_[d]);
-        }
-        uFo = uF;
-        P0o = P0;
-        opaque(uFo);
-        opaque(P0o);
-      }
-    };
-    // 3 w_a rho_c per weight class (|e_a|^2 = 1, 2)
-    const R b31 = (R)(3.0 * L::w(L::pfirst(0))) * rc[C], b32 = (R)(3.0 * L::w(L::pfirst(NP - 1))) * rc[C];
-    static_assert(L::c2(L::pfirst(0)) == 1 && L::c2(L::pfirst(NP - 1)) == 2, "pair order");
-    // g_a,b = v_a,b - w (dl + rho Pe) -+ 3 w rho e.u: each member in two multiply-adds, so the
-    // large even part of the equilibrium is never rounded on its own. Rounding it first
-    // (one ulp of the population, a biased error because w is inexact in binary) measured a
-    // 6x larger error of the 20000-step FP32 droplet against the oracle.
-    auto pair_g = [&](auto k_, R va, R vb, V2<R>& g, R& Fe, R& Fo) {
-      constexpr int K = decltype(k_)::value;
-      constexpr int a = L::pfirst(K);
-      R Pe, eu;
-      if constexpr (PT) {
-        Pe = pt(0, K);
-        eu = pt(1, K);
-        Fe = pt(2, K);
-        Fo = pt(3, K);
-      } else {
-        eu = dot(uo, std::integral_constant<int, a>{});
-        const R eF = dot(Fo_, std::integral_constant<int, a>{});
-        Pe = fmx((R)4.5 * eu, eu, P0o);
-        Fe = (R)L::w(a) * fmx((R)9 * eu, eF, (R)-3 * uFo);
-        Fo = (R)(3.0 * L::w(a)) * eF;
-      }
-      const R t = fmx(rc[C], Pe, dl[C]);
-      const R b3 = L::c2(a) == 1 ? b31 : b32;
-      const R mw = -(R)L::w(a);
-      g = fma2(v2(-b3, b3), v2(eu, eu), fma2(v2(mw, mw), v2(t, t), v2(va, vb)));
-    };
-    const R v0 = (R)ld_pop(fc + AA<Q>::template rd<0, PAR>(P, so));
-    const R g0 = fmx(-(R)L::w(0), fmx(rc[C], P0, dl[C]), v0);
-    R d0 = fmx(gkchi, F0, -om * g0);
-    R lm[L::NK];
-    if constexpr (MRT) {
-      refresh();
-      R cs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      R mq[L::NK];
+  for (int c = 0; c < NC; ++c) sp.dl[c] = dl[c];
+}
+
+// S6 of component C at one site, given the site's shared values: Guo-forced BGK or MRT
+// collision and the in-place AA write (see site_collide_m for the pair arrangement).
+template <int Q, int NC, class Prec, int MRT, int PAR, int C, int GLOBAL = 1, int PT = LBM_COLLIDE_PAIRS>
+__device__ __forceinline__ void comp_collide(const Params& P, typename Prec::S* __restrict__ f, const Site& s,
+                                             const SitePrep<Q, NC, typename Prec::R, PT>& sp,
+                                             typename Prec::S* fo = nullptr) {
+  using R = typename Prec::R;
+  using L = Lat<Q>;
+  constexpr int NP = L::NPAIR;
+  const R* rc = sp.rc;
+  const R* dl = sp.dl;
+  const R* u = sp.u;
+  const R* F = sp.F;
+  const R uF = sp.uF, P0 = sp.P0, F0 = sp.F0;
+  auto pt = [&](int i, int k) -> R { return sp.pt_r[PT ? i * NP + k : 0]; };
+  auto dot = [&](const R (&v)[3], auto a_) { return edot<Q, decltype(a_)::value>(v); };
+  const R om = PC<R>::omega(P);
+  const R gk = PC<R>::gk(P);
+  const R chi = sp.chis[C];
+  // Compiler-only barrier: the populations are re-read (from L1) rather than kept in
+  // registers from the moments pass, which would cost Q * NC registers.
+  asm volatile("" ::: "memory");
+  const R gkchi = gk * chi;
+  typename Prec::S* fc = comp_base<Q>(f, P, C);
+  // the new values go to the same slots of fo when given (a step out of place: each site
+  // writes exactly the slots it reads), else in place
+  typename Prec::S* fcw = comp_base<Q>(fo ? fo : f, P, C);
+  // Non-equilibrium part g = f - f_eq (stored variables) per pair: A is the even part of the
+  // equilibrium (one value for both members), B the odd part; the BGK + Guo change is
+  // d = gk chi Fb - omega g. For MRT a first pass accumulates the free-row moments of
+  // q = g + chi Fb / 2 in pair form (q_a + q_b = g_a + g_b + chi Fe, q_a - q_b =
+  // g_a - g_b + chi Fo; even rows through per-class sums, odd rows directly); the second
+  // pass re-reads the populations (L1), forms d and the MRT correction and stores. Keeping
+  // nothing per pair between the passes keeps the register count down.
+  // Per-pair values are the same for every component and both passes. With PT = 1 they
+  // come from the table computed once per site (4 registers per pair: about 9 instructions
+  // per pair and pass fewer, and fewer spills at 128 registers). With PT = 0 u, F and u.F
+  // pass through an empty asm, which makes them opaque per pass, so the values are
+  // recomputed from them (a few FMAs per pair) instead of held.
+  R uo[3], Fo_[3], uFo = uF, P0o = P0;
+  // The site's addresses are likewise made opaque per pass. Besides bounding the registers,
+  // this keeps the instruction stream of the collision the same in every kernel that
+  // inlines it: without it the fused and two-kernel steps were measured to differ in the
+  // last bit (the multiply-add contractions follow the instruction order).
+  Site so = s;
+  auto refresh = [&]() {
+    so = s;
+    opaque(so);
+    if constexpr (!PT) {  // with the table, u, F and u.F are not needed after it is filled
 #pragma unroll
-      for (int i = 0; i < L::NK; ++i) mq[i] = 0;
-      For<0, NP>::run([&]<int K>() {
+      for (int d = 0; d < 3; ++d) {
+        uo[d] = u[d];
+        Fo_[d] = F[d];
+        opaque(uo[d]);
+        opaque(Fo_[d]);
+      }
+      uFo = uF;
+      P0o = P0;
+      opaque(uFo);
+      opaque(P0o);
+    }
+  };
+  // 3 w_a rho_c per weight class (|e_a|^2 = 1, 2)
+  const R b31 = (R)(3.0 * L::w(L::pfirst(0))) * rc[C], b32 = (R)(3.0 * L::w(L::pfirst(NP - 1))) * rc[C];
+  static_assert(L::c2(L::pfirst(0)) == 1 && L::c2(L::pfirst(NP - 1)) == 2, "pair order");
+  // g_a,b = v_a,b - w (dl + rho Pe) -+ 3 w rho e.u: each member in two multiply-adds, so the
+  // large even part of the equilibrium is never rounded on its own. Rounding it first
+  // (one ulp of the population, a biased error because w is inexact in binary) measured a
+  // 6x larger error of the 20000-step FP32 droplet against the oracle.
+  auto pair_g = [&](auto k_, R va, R vb, V2<R>& g, R& Fe, R& Fo) {
+    constexpr int K = decltype(k_)::value;
+    constexpr int a = L::pfirst(K);
+    R Pe, eu;
+    if constexpr (PT) {
+      Pe = pt(0, K);
+      eu = pt(1, K);
+      Fe = pt(2, K);
+      Fo = pt(3, K);
+    } else {
+      eu = dot(uo, std::integral_constant<int, a>{});
+      const R eF = dot(Fo_, std::integral_constant<int, a>{});
+      Pe = fmx((R)4.5 * eu, eu, P0o);
+      Fe = (R)L::w(a) * fmx((R)9 * eu, eF, (R)-3 * uFo);
+      Fo = (R)(3.0 * L::w(a)) * eF;
+    }
+    const R t = fmx(rc[C], Pe, dl[C]);
+    const R b3 = L::c2(a) == 1 ? b31 : b32;
+    const R mw = -(R)L::w(a);
+    g = fma2(v2(-b3, b3), v2(eu, eu), fma2(v2(mw, mw), v2(t, t), v2(va, vb)));
+  };
+  const R v0 = (R)ld_pop(fc + AA<Q>::template rd<0, PAR>(P, so));
+  const R g0 = fmx(-(R)L::w(0), fmx(rc[C], P0, dl[C]), v0);
+  R d0 = fmx(gkchi, F0, -om * g0);
+  R lm[L::NK];
+  if constexpr (MRT) {
+    refresh();
+    R cs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    R mq[L::NK];
+#pragma unroll
+    for (int i = 0; i < L::NK; ++i) mq[i] = 0;
+    For<0, NP>::run([&]<int K>() {
+      constexpr int a = L::pfirst(K), b = L::opp(a);
+      V2<R> g;
+      R Fe, Fo;
+      pair_g(std::integral_constant<int, K>{}, (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, so)),
+             (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, so)), g, Fe, Fo);
+      // {chi Fe + (g_a + g_b), chi Fo + (g_a - g_b)}
+      const V2<R> q = fma2(v2(chi, chi), v2(Fe, Fo), add2(v2(g.x, g.x), v2(g.y, -g.y)));
+      cs[pclass<Q>(K)] += q.x;
+      const R qm = q.y;
+      For<0, L::NK>::run([&]<int I>() {
+        constexpr int k = L::krow(I);
+        constexpr int c = L::m(k, a);
+        if constexpr (row_parity<Q>(k) == -1 && c != 0) mq[I] = fmx((R)c, qm, mq[I]);
+      });
+    });
+    // lam_k (M q)_k over the free rows k
+    const R q0 = fmx((R)0.5 * chi, F0, g0);
+    For<0, L::NK>::run([&]<int I>() {
+      constexpr int k = L::krow(I);
+      R m = mq[I];
+      if constexpr (row_parity<Q>(k) == 1) {
+        if constexpr (L::m(k, 0) != 0) m = fmx((R)L::m(k, 0), q0, m);
+        For<1, 8>::run([&]<int CL>() {
+          if constexpr (crep<Q>(CL) >= 0) {
+            constexpr int c = L::m(k, L::pfirst(crep<Q>(CL)));
+            if constexpr (c != 0) m = fmx((R)c, cs[CL], m);
+          }
+        });
+      }
+      lm[I] = PC<R>::lam(P, I) * m;
+    });
+    For<0, L::NK>::run([&]<int I>() {
+      constexpr int k = L::krow(I);
+      if constexpr (row_parity<Q>(k) == 1 && L::m(k, 0) != 0) d0 = fmx(-(R)L::m(k, 0), lm[I], d0);
+    });
+    asm volatile("" ::: "memory");  // re-read the populations rather than keep them
+  }
+  // BGK + Guo (+ the MRT correction d_a -= sum_k M_ka lam_k (M q)_k: even part per pair
+  // class, odd part per pair), one rounding per stored population
+  R rest = dl[C];
+  refresh();
+  // Pairs in groups of G: the group's loads are issued before its first store. A warp issues
+  // in order and the loads stay behind earlier stores, so pair by pair every pair would wait
+  // for its own load; a group waits once. Each pair writes exactly the slots it reads (both
+  // steps of the AA pattern), so no store of a group touches a slot another pair reads.
+  constexpr int G = LBM_COLLIDE_GROUP < NP ? LBM_COLLIDE_GROUP : NP;
+  For<0, (NP + G - 1) / G>::run([&]<int GI>() {
+    R va[G], vb[G];
+    For<0, G>::run([&]<int J>() {
+      constexpr int K = GI * G + J;
+      if constexpr (K < NP) {
+        constexpr int a = L::pfirst(K), b = L::opp(a);
+        va[J] = (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, so));
+        vb[J] = (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, so));
+      }
+    });
+    For<0, G>::run([&]<int J>() {
+      constexpr int K = GI * G + J;
+      if constexpr (K < NP) {
         constexpr int a = L::pfirst(K), b = L::opp(a);
         V2<R> g;
         R Fe, Fo;
-        pair_g(std::integral_constant<int, K>{}, (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, so)),
-               (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, so)), g, Fe, Fo);
-        // {chi Fe + (g_a + g_b), chi Fo + (g_a - g_b)}
-        const V2<R> q = fma2(v2(chi, chi), v2(Fe, Fo), add2(v2(g.x, g.x), v2(g.y, -g.y)));
-        cs[pclass<Q>(K)] += q.x;
-        const R qm = q.y;
-        For<0, L::NK>::run([&]<int I>() {
-          constexpr int k = L::krow(I);
-          constexpr int c = L::m(k, a);
-          if constexpr (row_parity<Q>(k) == -1 && c != 0) mq[I] = fmx((R)c, qm, mq[I]);
-        });
-      });
-      // lam_k (M q)_k over the free rows k
-      const R q0 = fmx((R)0.5 * chi, F0, g0);
-      For<0, L::NK>::run([&]<int I>() {
-        constexpr int k = L::krow(I);
-        R m = mq[I];
-        if constexpr (row_parity<Q>(k) == 1) {
-          if constexpr (L::m(k, 0) != 0) m = fmx((R)L::m(k, 0), q0, m);
-          For<1, 8>::run([&]<int CL>() {
-            if constexpr (crep<Q>(CL) >= 0) {
-              constexpr int c = L::m(k, L::pfirst(crep<Q>(CL)));
-              if constexpr (c != 0) m = fmx((R)c, cs[CL], m);
+        pair_g(std::integral_constant<int, K>{}, va[J], vb[J], g, Fe, Fo);
+        // d = gk chi (Fe +- Fo) - omega g
+        V2<R> d = fma2(v2(gkchi, gkchi), add2(v2(Fe, Fe), v2(Fo, -Fo)), mul2(v2(-om, -om), g));
+        if constexpr (MRT) {
+          R ev = 0, od = 0;
+          For<0, L::NK>::run([&]<int I>() {
+            constexpr int k = L::krow(I);
+            constexpr int c = L::m(k, a);
+            if constexpr (c != 0) {
+              if constexpr (row_parity<Q>(k) == 1)
+                ev = fmx((R)c, lm[I], ev);
+              else
+                od = fmx((R)c, lm[I], od);
             }
           });
+          // d_a - (ev + od), d_b - (ev - od): the sums negated exactly
+          d = add2(d, add2(v2(-ev, -ev), v2(-od, od)));
         }
-        lm[I] = PC<R>::lam(P, I) * m;
-      });
-      For<0, L::NK>::run([&]<int I>() {
-        constexpr int k = L::krow(I);
-        if constexpr (row_parity<Q>(k) == 1 && L::m(k, 0) != 0) d0 = fmx(-(R)L::m(k, 0), lm[I], d0);
-      });
-      asm volatile("" ::: "memory");  // re-read the populations rather than keep them
-    }
-    // BGK + Guo (+ the MRT correction d_a -= sum_k M_ka lam_k (M q)_k: even part per pair
-    // class, odd part per pair), one rounding per stored population
-    R rest = dl[C];
-    refresh();
-    // Pairs in groups of G: the group's loads are issued before its first store. A warp issues
-    // in order and the loads stay behind earlier stores, so pair by pair every pair would wait
-    // for its own load; a group waits once. Each pair writes exactly the slots it reads (both
-    // steps of the AA pattern), so no store of a group touches a slot another pair reads.
-    constexpr int G = LBM_COLLIDE_GROUP < NP ? LBM_COLLIDE_GROUP : NP;
-    For<0, (NP + G - 1) / G>::run([&]<int GI>() {
-      R va[G], vb[G];
-      For<0, G>::run([&]<int J>() {
-        constexpr int K = GI * G + J;
-        if constexpr (K < NP) {
-          constexpr int a = L::pfirst(K), b = L::opp(a);
-          va[J] = (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, so));
-          vb[J] = (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, so));
-        }
-      });
-      For<0, G>::run([&]<int J>() {
-        constexpr int K = GI * G + J;
-        if constexpr (K < NP) {
-          constexpr int a = L::pfirst(K), b = L::opp(a);
-          V2<R> g;
-          R Fe, Fo;
-          pair_g(std::integral_constant<int, K>{}, va[J], vb[J], g, Fe, Fo);
-          // d = gk chi (Fe +- Fo) - omega g
-          V2<R> d = fma2(v2(gkchi, gkchi), add2(v2(Fe, Fe), v2(Fo, -Fo)), mul2(v2(-om, -om), g));
-          if constexpr (MRT) {
-            R ev = 0, od = 0;
-            For<0, L::NK>::run([&]<int I>() {
-              constexpr int k = L::krow(I);
-              constexpr int c = L::m(k, a);
-              if constexpr (c != 0) {
-                if constexpr (row_parity<Q>(k) == 1)
-                  ev = fmx((R)c, lm[I], ev);
-                else
-                  od = fmx((R)c, lm[I], od);
-              }
-            });
-            // d_a - (ev + od), d_b - (ev - od): the sums negated exactly
-            d = add2(d, add2(v2(-ev, -ev), v2(-od, od)));
-          }
-          const V2<R> o = add2(v2(va[J], vb[J]), d);
-          const R oa = o.x, ob = o.y;
-          if constexpr (sizeof(R) == 4) rest -= oa + ob;
-          store_pop<Prec, GLOBAL>(fcw + AA<Q>::template wr<a, PAR>(P, so), oa);
-          store_pop<Prec, GLOBAL>(fcw + AA<Q>::template wr<b, PAR>(P, so), ob);
-        }
-      });
+        const V2<R> o = add2(v2(va[J], vb[J]), d);
+        const R oa = o.x, ob = o.y;
+        if constexpr (sizeof(R) == 4) rest -= oa + ob;
+        store_pop<Prec, GLOBAL>(fcw + AA<Q>::template wr<a, PAR>(P, so), oa);
+        store_pop<Prec, GLOBAL>(fcw + AA<Q>::template wr<b, PAR>(P, so), ob);
+      }
     });
-    // The weights rounded to FP32 sum to 1 + 7.5e-9 (D2Q9) or 1 + 1.5e-8 (D3Q19), which makes
-    // every step scale the stored deviation rho_c - rho_ref_c by 1 + omega * that excess: a
-    // systematic drift of mass from vapour to liquid. The collision conserves each component's
-    // mass (the mass row is not relaxed and sum_a Fb_a = 0), so in FP32 the rest population is
-    // set from that invariant instead, leaving only unbiased rounding.
-    const R out0 = sizeof(R) == 4 ? rest : v0 + d0;
-    store_pop<Prec, GLOBAL>(fcw + AA<Q>::template wr<0, PAR>(P, s), out0);
   });
+  // The weights rounded to FP32 sum to 1 + 7.5e-9 (D2Q9) or 1 + 1.5e-8 (D3Q19), which makes
+  // every step scale the stored deviation rho_c - rho_ref_c by 1 + omega * that excess: a
+  // systematic drift of mass from vapour to liquid. The collision conserves each component's
+  // mass (the mass row is not relaxed and sum_a Fb_a = 0), so in FP32 the rest population is
+  // set from that invariant instead, leaving only unbiased rounding.
+  const R out0 = sizeof(R) == 4 ? rest : v0 + d0;
+  store_pop<Prec, GLOBAL>(fcw + AA<Q>::template wr<0, PAR>(P, s), out0);
+}
+
+// S4-S6 of one site given psi at the site (pn[0]) and its Q - 1 neighbours (pn[a] at x + e_a)
+// and the site's moments: total force, split, Guo-forced BGK or MRT collision, in-place AA
+// write. Everything is arranged over the pairs of opposite directions (a, b = opp(a)):
+//   * the equilibrium is w_a (dl_c + rho_c P_a) with P_a = Pe +- Po (even / odd parts of
+//     3 e.u + 9/2 (e.u)^2 - 3/2 u.u); its large even part w (dl_c + rho_c Pe) is the same for
+//     both members and is subtracted from each population inside a multiply-add, never
+//     rounded on its own;
+//   * the Guo term Fb_a = w_a [3 (e_a - u).F + 9 (e_a.u)(e_a.F)] = Fe +- Fo likewise;
+//   * the MRT correction acts on the free rows through pair sums (even rows, one coefficient
+//     per pair class) and pair differences (odd rows);
+//   * the change d_a of each population is formed in full before it is added to the stored
+//     value, so the population is rounded once.
+// In FP32 these keep the rounding of the large quantities out of the momentum balance; a
+// textbook per-direction evaluation lets that rounding drive a random walk of the total
+// momentum, and long runs of a liquid slab then drift measurably.
+template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1, int PT = LBM_COLLIDE_PAIRS>
+__device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S* __restrict__ f, const Site& s,
+                                               const typename Prec::R (&pn)[Q], const typename Prec::R (&dl)[NC],
+                                               const typename Prec::R (&j)[3], typename Prec::S* fo = nullptr) {
+  SitePrep<Q, NC, typename Prec::R, PT> sp;
+  site_prep<Q, NC, Prec, PT>(P, pn, dl, j, sp);
+  For<0, NC>::run([&]<int C>() { comp_collide<Q, NC, Prec, MRT, PAR, C, GLOBAL, PT>(P, f, s, sp, fo); });
 }
 
 // S1 and S4-S6 of one site (the moments, then the collision).
@@ -598,19 +696,51 @@ __global__ void __launch_bounds__(kBlock) k_psi(const Params P, const typename P
 }
 
 // Pass 2: S4-S6 of every site; psi of the neighbours from global memory.
-template <int Q, int NC, class Prec, int MRT, int PAR>
-__device__ __forceinline__ void collide_body(const Params& P, typename Prec::S* __restrict__ f,
-                                             const typename Prec::PsiT* __restrict__ psi, int x,
-                                             typename Prec::S* fo = nullptr) {
+// LBM_COLLIDE_NOINLINE = 1 keeps one site's collision out of line: the kernel's own state
+// does not stay live across it, which leaves its registers to the collision (fewer spills).
+#ifndef LBM_COLLIDE_NOINLINE
+#define LBM_COLLIDE_NOINLINE 0
+#endif
+template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1>
+__device__ __forceinline__ void collide_site(const Params& P, typename Prec::S* __restrict__ f,
+                                             const typename Prec::PsiT* __restrict__ psi, int x, int y, int z,
+                                             typename Prec::S* fo) {
   using R = typename Prec::R;
   using L = Lat<Q>;
   Site s;
-  s.set_xyz(P, x, blockIdx.y, blockIdx.z);
+  s.set_xyz(P, x, y, z);
   R pn[Q];
   pn[0] = (R)psi[s.idx];
 #pragma unroll
   for (int a = 1; a < Q; ++a) pn[a] = (R)psi[s.nb(P, L::e(a, 0), L::e(a, 1), L::e(a, 2))];
-  site_collide<Q, NC, Prec, MRT, PAR>(P, f, s, pn, fo);
+  site_collide<Q, NC, Prec, MRT, PAR, GLOBAL>(P, f, s, pn, fo);
+}
+template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1>
+__device__ __attribute__((noinline)) void collide_site_noinline(const Params& P, typename Prec::S* __restrict__ f,
+                                                                 const typename Prec::PsiT* __restrict__ psi, int x,
+                                                                 int y, int z, typename Prec::S* fo) {
+  collide_site<Q, NC, Prec, MRT, PAR, GLOBAL>(P, f, psi, x, y, z, fo);
+}
+// S1-S3 of one site into psi_out[site]; returns the status bits (0 when fine).
+template <int Q, int NC, class Prec, int PAR>
+__device__ __attribute__((noinline)) int psi_site_noinline(const Params& P, const typename Prec::S* __restrict__ f,
+                                                            typename Prec::PsiT* __restrict__ psi_out, int x, int y,
+                                                            int z) {
+  Site s;
+  s.set_xyz(P, x, y, z);
+  typename Prec::PsiT v;
+  const int e = site_psi<Q, NC, Prec, PAR>(P, f, s, v);
+  psi_out[s.idx] = v;
+  return e;
+}
+template <int Q, int NC, class Prec, int MRT, int PAR>
+__device__ __forceinline__ void collide_body(const Params& P, typename Prec::S* __restrict__ f,
+                                             const typename Prec::PsiT* __restrict__ psi, int x,
+                                             typename Prec::S* fo = nullptr) {
+  if constexpr (LBM_COLLIDE_NOINLINE)
+    collide_site_noinline<Q, NC, Prec, MRT, PAR>(P, f, psi, x, blockIdx.y, blockIdx.z, fo);
+  else
+    collide_site<Q, NC, Prec, MRT, PAR>(P, f, psi, x, blockIdx.y, blockIdx.z, fo);
 }
 
 template <int Q, int NC, class Prec, int MRT>
@@ -678,10 +808,11 @@ struct FusedArgs {
   int ntx, nty, nchunk, L;    // tiles along x and y (1 in 2-D), chunks and chunk length
   int silent_block;           // test hook: this block publishes no progress (-1: none)
   // plane-range form (k_fused3, D3Q19)
-  int mode;                   // 1 (or 0): tile columns (k_fused), 3: plane ranges (k_fused3)
+  int mode;                   // 1 (or 0): tile columns (k_fused), 3: plane ranges (k_fused3),
+                              // 4: plane ranges with trailing psi (k_trail3)
   const int* range;           // G + 1 range starts in the flattened (y, x) index of a plane
   const int* nbr;             // G x kF3MaxNbr workers owning neighbour sites, -1 padded
-  void* psi_ring;             // (kF3Ring + 2) psi planes
+  void* psi_ring;             // k_fused3: (kF3Ring + 2) psi planes; k_trail3: two psi fields
   int G, smax;                // workers (two per CTA), largest range
 };
 
@@ -1096,6 +1227,7 @@ __global__ void k_mass_final(const double* partial, int nblocks, int nc, MassShi
 }  // namespace lbm
 
 #include "lbm_fused3.cuh"
+#include "lbm_trail3.cuh"
 
 namespace lbm {
 
@@ -1181,6 +1313,32 @@ struct Launch {
                                          dim3(kF3Threads), args, smem, s);
     }
   }
+  static int trail3_max_blocks() {
+    if constexpr (Q != 19) {
+      return 0;
+    } else {
+      int nb = 0, dev = 0, sms = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trail3<NC, Prec, MRT>, kT3Threads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+      }
+      return nb * sms;
+    }
+  }
+  static cudaError_t trail3(const Params& P, void* f, int* st, long long* t_dev, const FusedArgs& A, cudaStream_t s) {
+    if constexpr (Q != 19) {
+      return cudaErrorNotSupported;
+    } else {
+      S* fp = (S*)f;
+      Params Pc = P;
+      FusedArgs Ac = A;
+      void* args[] = {(void*)&Pc, (void*)&fp, (void*)&st, (void*)&t_dev, (void*)&Ac};
+      return cudaLaunchCooperativeKernel((const void*)k_trail3<NC, Prec, MRT>, dim3((unsigned)A.G),
+                                         dim3(kT3Threads), args, 0, s);
+    }
+  }
   static void init(const Params& P, void* f, const double* rho, const double* u, cudaStream_t s) {
     k_init<Q, NC, Prec><<<blocks(P), kBlock, 0, s>>>(P, (S*)f, rho, u);
   }
@@ -1206,7 +1364,8 @@ struct Launch {
     static const Ops ops = {psi,           collide,           fused,        fused_max_blocks, fused3,
                             fused3_max_blocks, init,          get_f,        set_f,            fields,
                             mass,          (int)sizeof(S),    (int)sizeof(PsiT), (int)sizeof(R), Fused<Q>::TX,
-                            Fused<Q>::TY,  Fused<Q>::P,       kF3WorkersPerCta,  kF3FlagSets,       collide_oop};
+                            Fused<Q>::TY,  Fused<Q>::P,       kF3WorkersPerCta,  kF3FlagSets,       collide_oop,
+                            trail3,        trail3_max_blocks};
     return &ops;
   }
 };

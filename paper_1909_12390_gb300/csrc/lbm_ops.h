@@ -36,6 +36,10 @@ struct Ops {
   // the collide pass reading the state in fin and writing the next one to fout
   void (*collide_oop)(const Params&, const void* fin, void* fout, const void* psi, const int* status,
                       long long* t_dev, int parity, cudaStream_t);
+  // trailing fused step (D3Q19 only; cudaErrorNotSupported / 0 otherwise): psi of the step
+  // from A.psi_ring[t & 1], psi of the next step into A.psi_ring[(t + 1) & 1]
+  cudaError_t (*trail3)(const Params&, void* f, int* status, long long* t_dev, const FusedArgs&, cudaStream_t);
+  int (*trail3_max_blocks)();  // co-resident CTAs of the trailing step on this device
 };
 
 // one translation unit per lattice, storage type and collision

@@ -1,0 +1,279 @@
+// Trailing fused D3Q19 step (k_trail3): one persistent cooperative launch per step, in which
+// the pseudo-potential of the NEXT step trails the collision of this one.
+//
+// Step t needs psi(t) at every site before any collision, and psi(t) needs the densities of
+// the state at t. Here psi(t) was finished by the launch of step t - 1 (or by a pseudo-potential
+// pass before the first step), so the collisions of step t wait for nothing. CTA b owns the
+// contiguous range [range[b], range[b+1]) of the flattened (y, x) index of a z plane and
+// marches z = 0 .. nz-1; iteration k
+//   1. (one thread) prefetches into L2, with bulk prefetches, the slots that the collision of
+//      plane k + LBM_T3_PREFETCH will read;
+//   2. collides and streams plane k of its range in place (psi(t) of the 18 neighbours from
+//      the current buffer, read-only in this launch), then arrives on the plane's mbarrier;
+//   3. (one thread) publishes, with st.release.gpu, the last plane that all of its threads have
+//      collided (mbarrier phases it finds complete);
+//   4. computes psi(t + 1) of plane p = k - LAG of its range into the other buffer: the
+//      densities of the state at t + 1 at a site are sums over slots written by the collisions
+//      of planes p - 1 .. p + 1 of this CTA and of the CTAs owning neighbour sites, so the
+//      stage first waits (bounded) for its own CTA's mbarrier of plane p + 1 and for the
+//      neighbours' published progress >= p + 1. Those slots were written LAG - 1 .. LAG + 1
+//      iterations earlier; with every CTA marching the same planes, the grid touches a few
+//      planes meanwhile (15 MB each at 256^2 sites, three FP32 D3Q19 components), so the
+//      re-reads come from L2.
+// After the march the stages of planes nz - LAG .. nz - 1 and of plane 0 (which needs plane
+// nz - 1) follow once every neighbour has finished. The result of a step is the same, bit for
+// bit, as that of the two-kernel step: the collision is the same per-site code, and psi(t+1)
+// of a site is site_psi over the same slots.
+//
+// Each site reads and writes only its own set of slots (AA pattern), so a site's collision
+// never disturbs another site's populations; the only cross-site dependency is psi, and psi(t)
+// is complete before the launch. The waits go only backwards in the march (a stage of plane p
+// waits for collisions of planes <= p + 1 < k, published before the waiter's iteration), and
+// the cooperative launch makes all CTAs co-resident, so the pipeline cannot deadlock; every
+// wait is bounded anyway (kSpinLimit polls), after which the step reports a timeout.
+// Errors of the psi(t + 1) stage (EOS domain, non-finite) are collected in A.pending and folded
+// into the status word by the last CTA: step t completed, and the next step is the failing one.
+#pragma once
+
+namespace lbm {
+
+#ifndef LBM_T3_THREADS
+#define LBM_T3_THREADS 448
+#endif
+constexpr int kT3Threads = LBM_T3_THREADS;  // 14 warps, one site each of a 431-site range
+// registers per thread: the warps of a CTA are spread over the SM's four sub-partitions, each
+// with 16 K registers, so the busiest sub-partition (ceil(warps / 4) warps) bounds them: 128 for
+// 14 warps, 168 for 12
+#define LBM_T3_WPS ((LBM_T3_THREADS / 32 + 3) / 4)
+#ifndef LBM_T3_MAXREG
+#define LBM_T3_MAXREG (16384 / (LBM_T3_WPS * 32) / 8 * 8 > 255 ? 255 : 16384 / (LBM_T3_WPS * 32) / 8 * 8)
+#endif
+static_assert(kT3Threads % 32 == 0 && kT3Threads <= 1024, "trailing step block size");
+// planes between a plane's collision and its psi(t + 1) stage
+#ifndef LBM_T3_LAG
+#define LBM_T3_LAG 3
+#endif
+constexpr int kT3Lag = LBM_T3_LAG;
+static_assert(kT3Lag >= 2, "the psi stage of plane k - LAG needs plane k - LAG + 1 collided by the neighbours");
+// planes ahead of the collision that are prefetched into L2 (0: none)
+#ifndef LBM_T3_PREFETCH
+#define LBM_T3_PREFETCH 0
+#endif
+constexpr int kT3Prefetch = LBM_T3_PREFETCH;
+// population stores: 1 evict-first (st.global.cs), 2 write-back (st.global.wb, kept in L2 for the
+// psi stage)
+#ifndef LBM_T3_CS
+#define LBM_T3_CS 2
+#endif
+constexpr int kT3Ring = 8;  // mbarriers, plane k on k % kT3Ring
+static_assert(kT3Ring >= kT3Lag + 2, "mbarrier ring shorter than the drift the waits allow");
+
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(b)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(b))
+               : "memory");
+}
+// true once the phase with the given parity has completed (acquire at CTA scope)
+__device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity) {
+  unsigned r;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, "
+      "p;\n\t}"
+      : "=r"(r)
+      : "r"((unsigned)__cvta_generic_to_shared(b)), "r"(parity)
+      : "memory");
+  return r != 0;
+}
+// L2 prefetch of the 16-byte units inside [lo, hi) (generic addresses of global memory): the
+// start is rounded up and the end down to 16 bytes, so the prefetch never leaves the range
+__device__ __forceinline__ void bulk_prefetch_l2(const void* lo, const void* hi) {
+  const unsigned long long a = ((unsigned long long)lo + 15) & ~15ull, e = (unsigned long long)hi & ~15ull;
+  if (e <= a) return;
+  asm volatile(
+      "{\n\t.reg .u64 g;\n\tcvta.to.global.u64 g, %0;\n\tcp.async.bulk.prefetch.L2.global [g], %1;\n\t}" ::"l"(a),
+      "r"((unsigned)(e - a))
+      : "memory");
+}
+
+// L2 prefetch of the slots the collision of plane z of sites [r0, r0 + S) reads: at even steps
+// the range's own slots; at odd steps slot (x + e_b, b) for array b, i.e. plane z + e_b,z and the
+// range widened by one row and one site on each side. Out of line: its 57 address streams would
+// otherwise hold registers across the whole march.
+template <int NC, class Prec, int PAR>
+__device__ __attribute__((noinline)) void trail3_prefetch(const Params& P, const typename Prec::S* f, int r0, int S,
+                                                           int z) {
+  constexpr int Q = 19;
+  using L = Lat<Q>;
+  using S_ = typename Prec::S;
+  const int nx = P.nx, nz = P.nz, nxy = P.nx * P.ny;
+  const int lo = PAR ? r0 - nx - 1 : r0, hi = PAR ? r0 + S + nx + 1 : r0 + S;
+  const int lc = lo < 0 ? 0 : lo, hc = hi > nxy ? nxy : hi;
+#pragma unroll 1
+  for (int C = 0; C < NC; ++C) {
+    const S_* fc = f + (size_t)C * Q * P.N;
+#pragma unroll 1
+    for (int B = 0; B < Q; ++B) {
+      int zz = z + (PAR ? L::e(B, 2) : 0);
+      zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+      const S_* p0 = fc + (size_t)B * P.N + (size_t)zz * nxy;
+      bulk_prefetch_l2(p0 + lc, p0 + hc);
+    }
+  }
+}
+
+template <int NC, class Prec, int MRT, int PAR>
+__device__ __forceinline__ void trail3_body(const Params& P, typename Prec::S* __restrict__ f, int* status,
+                                            long long* t_dev, const FusedArgs& A, unsigned long long t) {
+  constexpr int Q = 19;
+  using R = typename Prec::R;
+  using S_ = typename Prec::S;
+  using PsiT = typename Prec::PsiT;
+  using L = Lat<Q>;
+  __shared__ unsigned long long mbar[kT3Ring];
+  __shared__ int nbr[kF3MaxNbr];
+  __shared__ int n_nbr;
+
+  const int tid = threadIdx.x, b = blockIdx.x;
+  const int r0 = A.range[b], S = A.range[b + 1] - r0;
+  const int nx = P.nx, nz = P.nz, nxy = P.nx * P.ny;
+  // progress value: planes collided + 1, at most nz + 1 in a launch
+  const unsigned long long base = t * (unsigned long long)(nz + 2);
+  const PsiT* __restrict__ psi_cur = (const PsiT*)A.psi_ring + (size_t)(t & 1) * P.N;
+  PsiT* psi_next = (PsiT*)A.psi_ring + (size_t)((t + 1) & 1) * P.N;
+  if (tid == 0) {
+    for (int i = 0; i < kT3Ring; ++i) mbar_init(&mbar[i], (unsigned)blockDim.x);
+    int n = 0;
+    while (n < kF3MaxNbr && A.nbr[b * kF3MaxNbr + n] >= 0) {
+      nbr[n] = A.nbr[b * kF3MaxNbr + n];
+      ++n;
+    }
+    n_nbr = n;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  int err = 0;
+  bool ok = true;
+  auto prefetch = [&](int z) { trail3_prefetch<NC, Prec, PAR>(P, f, r0, S, z); };
+  // the per-site work is out of line: the march's own state then does not stay live across the
+  // collision's registers (the collision spills 8-24 bytes per site instead of several hundred)
+  auto collide = [&](int z) {
+#pragma unroll 1
+    for (int i = tid; i < S; i += kT3Threads) {
+      const int xy = r0 + i;
+      collide_site_noinline<Q, NC, Prec, MRT, PAR, LBM_T3_CS>(P, f, psi_cur, xy % nx, xy / nx, z, nullptr);
+    }
+  };
+  auto stage = [&](int z) {
+#pragma unroll 1
+    for (int i = tid; i < S; i += kT3Threads) {
+      const int xy = r0 + i;
+      err |= psi_site_noinline<Q, NC, Prec, 1 - PAR>(P, f, psi_next, xy % nx, xy / nx, z);
+    }
+  };
+  // this CTA's collisions of plane z (and of every plane before it) are complete
+  auto wait_cta = [&](int z) {
+    unsigned it = 0;
+    while (!mbar_test(&mbar[z % kT3Ring], (unsigned)((z / kT3Ring) & 1))) {
+      if (++it > kSpinLimit) {
+        ok = false;
+        return;
+      }
+    }
+  };
+  // every neighbour CTA has collided plane z (lanes poll one neighbour each, the warp waits)
+  auto wait_nbrs = [&](int z) {
+    const int lane = tid & 31;
+    bool mine = true;
+    if (ok && lane < n_nbr) {
+      const unsigned long long target = base + (unsigned long long)z + 1;
+      const unsigned long long* fl = &A.flags[nbr[lane]];
+      unsigned it = 0;
+      while (ld_acquire_u64(fl) < target) {
+        if (++it > kSpinLimit) {
+          mine = false;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __syncwarp();  // orders the warp's later loads after the polling lanes' acquires
+    ok = __all_sync(0xffffffffu, mine) && ok;
+  };
+  int pub = -1;  // last plane published (thread 0)
+  auto publish = [&](int upto) {
+    bool adv = false;
+    while (pub < upto && mbar_test(&mbar[(pub + 1) % kT3Ring], (unsigned)(((pub + 1) / kT3Ring) & 1))) {
+      ++pub;
+      adv = true;
+    }
+    if (adv && b != A.silent_block) st_release_u64(&A.flags[b], base + (unsigned long long)pub + 1);
+  };
+
+  if (kT3Prefetch > 0 && tid == 0)
+    for (int z = 0; z < kT3Prefetch && z < nz; ++z) prefetch(z);
+  for (int k = 0; k < nz; ++k) {
+    if (kT3Prefetch > 0 && tid == 0 && k + kT3Prefetch < nz) prefetch(k + kT3Prefetch);
+    collide(k);
+    mbar_arrive(&mbar[k % kT3Ring]);
+    if (tid == 0) publish(k);
+    const int p = k - kT3Lag;
+    if (p >= 1 && p <= nz - 2) {
+      wait_cta(p + 1);
+      wait_nbrs(p + 1);
+      if (!__all_sync(0xffffffffu, ok)) ok = false;
+      if (ok) stage(p);
+    }
+  }
+  // the planes whose stage needs the end of the march: nz - LAG .. nz - 1, and plane 0 (it
+  // reads slots that plane nz - 1's collision writes)
+  wait_cta(nz - 1);
+  if (tid == 0) {
+    unsigned it = 0;
+    while (pub < nz - 1 && ok) {
+      publish(nz - 1);
+      if (pub < nz - 1 && ++it > kSpinLimit) ok = false;
+    }
+  }
+  wait_nbrs(nz - 1);
+  ok = __all_sync(0xffffffffu, ok);
+  if (ok) {
+    for (int p = nz - kT3Lag < 1 ? 1 : nz - kT3Lag; p < nz; ++p) stage(p);
+    stage(0);
+  }
+  if (!ok) err |= ST_TIMEOUT;
+  // finish: the last CTA of the launch folds the pending status and advances the step
+  if (err) atomicOr(A.pending, err);
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(A.done, 1u);
+    if (prev == gridDim.x - 1) {
+      __threadfence();
+      const int pend = *(volatile int*)A.pending;
+      // the collisions of step t are complete unless a wait timed out (state undefined then);
+      // a psi error belongs to step t + 1, which becomes the failing step
+      if (!(pend & ST_TIMEOUT)) *t_dev += 1;
+      if (pend) *status |= pend;
+      *A.pending = 0;
+      *A.done = 0;
+    }
+  }
+}
+
+template <int NC, class Prec, int MRT>
+__global__ void __maxnreg__(LBM_T3_MAXREG)
+    k_trail3(const Params P, typename Prec::S* __restrict__ f, int* status, long long* t_dev, const FusedArgs A) {
+  if (*(volatile int*)status) return;  // a previous step failed: do nothing
+  const unsigned long long t = (unsigned long long)*(volatile long long*)t_dev;
+  if (t & 1)
+    trail3_body<NC, Prec, MRT, 1>(P, f, status, t_dev, A, t);
+  else
+    trail3_body<NC, Prec, MRT, 0>(P, f, status, t_dev, A, t);
+}
+
+}  // namespace lbm

@@ -24,12 +24,13 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_init", "lbm_step"
            "lbm_fields", "lbm_mass", "lbm_get_f", "lbm_set_f", "lbm_state_bytes", "lbm_save",
            "lbm_restore", "lbm_last_error", "lbm_scale_to_lattice", "lbm_profile",
            "lbm_profile_read", "lbm_set_path", "lbm_get_path", "lbm_get_fused_kind", "lbm_test_silence_block",
+
            "lbm_step_static", "lbm_step_static_error", "lbm_batch_create", "lbm_batch_destroy",
            "lbm_batch_init", "lbm_batch_step", "lbm_batch_case_status", "lbm_batch_fields",
            "lbm_batch_get_f", "lbm_batch_tune", "lbm_batch_tune_report", "lbm_batch_sites",
            "lbm_batch_last_error", "lbm_record", "lbm_adjoint", "lbm_flash", "lbm_flash_error", "lbm_diagnostics")
 STATIC_MAX_SITES = 1048576
-PATH_AUTO, PATH_TWO_KERNEL, PATH_FUSED = 0, 1, 2
+PATH_AUTO, PATH_TWO_KERNEL, PATH_FUSED, PATH_TRAILING = 0, 1, 2, 3
 FUSED_TILES, FUSED_PLANES = 1, 3
 SPLIT_VOLATILITY, SPLIT_GONG = 0, 1
 

@@ -53,3 +53,58 @@ def random_rho(c, grid, seed):
     lo = np.array(c["rho_v"]).reshape((-1,) + (1,) * len(grid))
     hi = np.array(c["rho_l"]).reshape((-1,) + (1,) * len(grid))
     return lo + (hi - lo) * u
+
+
+def _erode(liq, e):
+    """(all-liquid, any-liquid) over the periodic L-infinity box of half-width e."""
+    all_l, any_l = liq.copy(), liq.copy()
+    for axis in range(liq.ndim):
+        a2, b2 = np.ones_like(all_l), np.zeros_like(any_l)
+        for d in range(-e, e + 1):
+            a2 &= np.roll(all_l, d, axis=axis)
+            b2 |= np.roll(any_l, d, axis=axis)
+        all_l, any_l = a2, b2
+    return all_l, any_l
+
+
+def bulk_masks(rho, erode=8):
+    """Bulk liquid and vapour cells of a state: farther than `erode` cells (L-infinity) from the
+    (max + min) / 2 contour of the total density."""
+    tot = rho.sum(axis=0)
+    liq = tot > 0.5 * (tot.max() + tot.min())
+    all_l, any_l = _erode(liq, erode)
+    return all_l, ~any_l
+
+
+def composition_profile_loss(rho, target, M, erode=8):
+    """The adjoint workload's loss and its gradient with respect to rho (numpy, FP64):
+    L = sum_i (x_i - x_i^T)^2 + sum_i (y_i - y_i^T)^2 + mean_x (rho(x) - rho^T(x))^2, with x, y the
+    molar compositions of the mean bulk liquid / vapour partial densities (each state its own
+    bulk masks) and rho the total density. The masks are piecewise constant in rho, so the
+    gradient treats them as fixed."""
+    M = np.asarray(M, dtype=float)
+    nc = rho.shape[0]
+    shp = (nc,) + (1,) * (rho.ndim - 1)
+
+    def comp(r, mask):
+        rbar = np.array([r[c][mask].mean() for c in range(nc)])
+        n = rbar / M
+        return n / n.sum(), n.sum(), int(mask.sum())
+
+    bl, bv = bulk_masks(rho, erode)
+    tl, tv = bulk_masks(target, erode)
+    x, nl, Nl = comp(rho, bl)
+    y, nv, Nv = comp(rho, bv)
+    xT, _, _ = comp(target, tl)
+    yT, _, _ = comp(target, tv)
+    tot, totT = rho.sum(0), target.sum(0)
+    N = tot.size
+    L = float(np.sum((x - xT) ** 2) + np.sum((y - yT) ** 2) + np.mean((tot - totT) ** 2))
+    g = np.broadcast_to(2.0 * (tot - totT) / N, rho.shape).copy()
+    for comp_, ref, n, cnt, mask in ((x, xT, nl, Nl, bl), (y, yT, nv, Nv, bv)):
+        # d comp_i / d rho_c(site) = (delta_ic - comp_i) / (n M_c cnt) on the bulk cells
+        w = 2.0 * (comp_ - ref)
+        for c in range(nc):
+            dc = (w[c] - np.dot(w, comp_)) / (n * M[c] * cnt)
+            g[c][mask] += dc
+    return L, g

@@ -24,3 +24,31 @@ def test_ambiguous_least_volatile_component_is_an_error(gamma):
 def test_pair_coefficient_is_set_symmetrically():
     k = _kij({"components": [0, 0, 0], "pair": (0, 2)}, 0.02)
     assert k[0, 2] == k[2, 0] == 0.02 and np.count_nonzero(k) == 2
+
+
+def test_workload_loss_gradient_matches_the_closed_form():
+    """The torch loss of the adjoint workload (losses.composition_profile_loss) and its autograd
+    gradient against the test helpers' numpy closed form (lbm_cases.composition_profile_loss),
+    written independently, on a droplet and a shifted target."""
+    import json
+    import os
+
+    import torch
+
+    import lbm_inputs
+    from conftest import GOLDEN
+    from lbm_cases import composition_profile_loss as np_loss
+    from paper_1909_12390_gb300.losses import composition_profile_loss
+
+    with open(os.path.join(GOLDEN, "cases.json")) as fh:
+        c = json.load(fh)["c5"]
+    grid = (40, 48)
+    rho = lbm_inputs.ball_fields(grid, c["rho_l"], c["rho_v"], 12.0, 4.0)
+    tgt = lbm_inputs.ball_fields(grid, c["rho_l"], c["rho_v"], 12.5, 4.0) * np.array([1.01, 0.99]).reshape(2, 1, 1)
+    M = [d["M"] for d in c["components"]]
+    L0, g0 = np_loss(rho, tgt, M)
+    r = torch.tensor(rho, requires_grad=True)
+    L = composition_profile_loss(r, torch.tensor(tgt), M)
+    L.backward()
+    assert float(L) == pytest.approx(L0, rel=1e-12)
+    assert np.max(np.abs(r.grad.numpy() - g0)) < 1e-12 * np.max(np.abs(g0))

@@ -188,3 +188,64 @@ def test_adjoint_full_workload_against_stored_duals(case5):
           % (dk12, ref["adjoint_dk12"], ds, ref["adjoint_ds"], t_plain, t_fwd, t_adj, t_adj / t_plain))
     assert dk12 == pytest.approx(float(ref["adjoint_dk12"]), rel=5e-3)
     assert ds == pytest.approx(float(ref["adjoint_ds"]), rel=5e-3)
+
+
+def test_workload_loss_gradient_against_oracle_duals(case5):
+    """The adjoint workload as stated: D2Q9 BGK binary droplet 256^2, FP32 forward with the FP64
+    EOS, 3000 steps, checkpoints every 55 steps; loss = squared errors of the bulk liquid and
+    vapour molar compositions plus the mean squared error of the density profile against a
+    target run at zeta_12 = 0.02 (paper_1909_12390_gb300.losses); gradient with respect to
+    zeta_12 and the split-factor scale s at zeta_12 = 0, s = 1 through LatticeRun, against the
+    FP64 oracle's dual numbers with the oracle's own target run (tests/golden/make_long_runs.py).
+    The loss compares two states that differ only through zeta_12, so its terms are differences
+    of nearly equal quantities (|x - x^T| ~ 1e-3) and carry the FP32 state error (~1e-5 of the
+    densities) magnified about a hundredfold: tolerance 2e-2. Prints the cost of the recorded
+    forward run and the backward pass relative to a plain forward run."""
+    import time
+
+    import torch
+    p = os.path.join(GOLDEN, "long_runs.npz")
+    ref = dict(np.load(p)) if os.path.exists(p) else {}
+    if "loss_dk12" not in ref:
+        pytest.skip("long_runs.npz has no workload-loss reference")
+    from paper_1909_12390_gb300 import lbm
+    from paper_1909_12390_gb300.autograd import LatticeRun
+    from paper_1909_12390_gb300.losses import composition_profile_loss
+    c = case5
+    shape = tuple(c["shape"])
+    grid = tuple(reversed(shape))
+    rho0 = lbm_inputs.ball_fields(grid, c["rho_l"], c["rho_v"], c["init"]["radius"], 4.0)
+    steps, K = int(ref["loss_steps"]), c["checkpoint_every"]
+    kt = float(c["target_k12"])
+    tgt = lbm.Lattice(shape, comps_of(c), T=c["T"], tau=c["tau"], gamma=c["gamma"],
+                      kij=np.array([[0.0, kt], [kt, 0.0]]), beta=c["beta"], G=c["G"], precision=FP32S)
+    tgt.init(rho0)
+    tgt.step(1)
+    tgt.init(rho0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tgt.step(steps)
+    t_plain = time.perf_counter() - t0
+    target = tgt.fields(u=False, p=False, psi=False)["rho"]
+    tgt.close()
+    ys, xs = ref["loss_target_sites"]
+    assert float(np.max(np.abs(target[:, ys, xs] - ref["loss_target_rho"]) / ref["loss_target_rho"].sum(0))) < 2e-4
+    spec = dict(shape=shape, components=comps_of(c), T=c["T"], tau=c["tau"], gamma=c["gamma"], beta=c["beta"],
+                G=c["G"], steps=steps, checkpoint_every=K, rho0=rho0, precision=lbm.FP32_SHIFTED, pair=(0, 1),
+                least_volatile=int(c["least_volatile"]))
+    zeta = torch.tensor(0.0, dtype=torch.float64, requires_grad=True)
+    s = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    t0 = time.perf_counter()
+    rho = LatticeRun.apply(zeta, s, spec)
+    t_rec = time.perf_counter() - t0
+    L = composition_profile_loss(rho, torch.from_numpy(target), [d["M"] for d in c["components"]])
+    t0 = time.perf_counter()
+    L.backward()
+    t_back = time.perf_counter() - t0
+    print("workload loss: L %.6e (oracle %.6e); dL/dk12 %.6e (oracle %.6e); dL/ds %.6e (oracle %.6e); "
+          "forward %.3f s, recorded forward %.3f s, backward %.3f s: (record + backward) / forward = %.2f"
+          % (float(L), float(ref["loss_value"]), zeta.grad.item(), float(ref["loss_dk12"]), s.grad.item(),
+             float(ref["loss_ds"]), t_plain, t_rec, t_back, (t_rec + t_back) / t_plain))
+    assert float(L) == pytest.approx(float(ref["loss_value"]), rel=2e-2)
+    assert zeta.grad.item() == pytest.approx(float(ref["loss_dk12"]), rel=2e-2)
+    assert s.grad.item() == pytest.approx(float(ref["loss_ds"]), rel=2e-2)

@@ -25,7 +25,45 @@ def _semi_axis(prof, thr):
     return 0.5 * (right - left)
 
 
-@pytest.mark.parametrize("row", [r for r in read_table("ellipse_periods.txt") if r[0] <= 300])
+def _ellipse_setup(nx):
+    """C3/nC5 at 580 degR and 70 psia, flash phase densities and gamma, and the droplet of Eq.
+    ellipsedroplet (h = 0.9, R0 = 0.15 nx, W = 4, liquid inside) on an nx x nx grid."""
+    t = {r[0]: th.Component(r[0], r[2], r[1], r[3], r[4]) for r in read_table("table1_components.txt")}
+    lb, ts, ps = th.lattice_components([t["C3"], t["nC5"]])
+    T, P = 580.0 * ts, 70.0 * ps
+    fr = th.flash(lb, [[0, 0], [0, 0]], T, P, [0.4, 0.6])
+    rl, rv, _, _ = th.phase_partial_densities(lb, T, P, 1.0, fr)
+    g, _ = th.gamma_coefficients(rl, rv, fr.K)
+    R0, h = 0.15 * nx, 0.9
+    yy, xx = np.mgrid[0:nx, 0:nx] + 0.5
+    r = np.sqrt((xx - nx / 2) ** 2 + ((yy - nx / 2) / h) ** 2)
+    rho = np.stack([0.5 * (rl[i] + rv[i]) - 0.5 * (rl[i] - rv[i]) * np.tanh(2 * (r - R0) / 4.0) for i in range(2)])
+    return lb, T, g, rl, rv, rho
+
+
+def test_elliptical_droplet_matches_oracle():
+    """The ellipse workload (nx = 200) against the FP64 oracle after 300 steps: every density
+    within 1e-10."""
+    import oracle
+    from paper_1909_12390_gb300 import lbm
+    nx, steps = 200, 300
+    lb, T, g, rl, rv, rho = _ellipse_setup(nx)
+    gpu = lbm.Lattice((nx, nx), [(k.Tc, k.pc, k.omega, k.M) for k in lb], T=T, tau=0.59, gamma=g, beta=1.815,
+                      G=-1.0, precision=lbm.FP64)
+    gpu.init(rho)
+    gpu.step(steps)
+    rg = gpu.fields(u=False, p=False, psi=False)["rho"]
+    gpu.close()
+    ocase = oracle.Case(Q=9, shape=(nx, nx), Tc=[k.Tc for k in lb], pc=[k.pc for k in lb],
+                        omega=[k.omega for k in lb], M=[k.M for k in lb], T=T, tau=0.59, gamma=list(g),
+                        beta=1.815, G=-1.0)
+    ro = oracle.fields(ocase, oracle.step(ocase, oracle.equilibrium(ocase, rho), steps)).rho
+    err = float(np.max(np.abs(rg - ro) / ro))
+    print("ellipse nx %d, %d steps: max rel err %.3e" % (nx, steps, err))
+    assert err < 1e-10
+
+
+@pytest.mark.parametrize("row", read_table("ellipse_periods.txt"))
 def test_elliptical_droplet_period(row):
     """C3/nC5 at 580 degR and 70 psia (density ratio ~58), beta = 1.815, tau = 0.59, the
     droplet of Eq. ellipsedroplet with h = 0.9, R0 = 0.15 nx and W = 4 (liquid inside: the
@@ -35,30 +73,23 @@ def test_elliptical_droplet_period(row):
     from paper_1909_12390_gb300 import lbm
     nx, theory, model, _ = row
     nx = int(nx)
-    t = {r[0]: th.Component(r[0], r[2], r[1], r[3], r[4]) for r in read_table("table1_components.txt")}
-    lb, ts, ps = th.lattice_components([t["C3"], t["nC5"]])
-    T, P = 580.0 * ts, 70.0 * ps
-    fr = th.flash(lb, [[0, 0], [0, 0]], T, P, [0.4, 0.6])
-    rl, rv, _, _ = th.phase_partial_densities(lb, T, P, 1.0, fr)
-    g, _ = th.gamma_coefficients(rl, rv, fr.K)
+    lb, T, g, rl, rv, rho = _ellipse_setup(nx)
     assert 50 < sum(rl) / sum(rv) < 65  # "about 58"
-    R0, h = 0.15 * nx, 0.9
-    yy, xx = np.mgrid[0:nx, 0:nx] + 0.5
-    r = np.sqrt((xx - nx / 2) ** 2 + ((yy - nx / 2) / h) ** 2)
-    rho = np.stack([0.5 * (rl[i] + rv[i]) - 0.5 * (rl[i] - rv[i]) * np.tanh(2 * (r - R0) / 4.0) for i in range(2)])
     gpu = lbm.Lattice((nx, nx), [(k.Tc, k.pc, k.omega, k.M) for k in lb], T=T, tau=0.59, gamma=g, beta=1.815, G=-1.0)
     gpu.init(rho)
     thr = 0.5 * (sum(rl) + sum(rv))
     times, diff = [], []
-    for _ in range(int(4.2 * model) // 10):
-        gpu.step(10)
+    every = 10 if nx <= 300 else 20  # samples per period stay above 200
+    for _ in range(int(4.2 * model) // every):
+        gpu.step(every)
         d = gpu.fields(u=False, p=False, psi=False)["rho"].sum(0)
         ax = _semi_axis(d[nx // 2 - 1:nx // 2 + 1].mean(0), thr)
         ay = _semi_axis(d[:, nx // 2 - 1:nx // 2 + 1].mean(1), thr)
         times.append(gpu.time)
         diff.append(ax - ay)
     gpu.close()
-    zc = [times[i] + 10 * diff[i] / (diff[i] - diff[i + 1]) for i in range(len(diff) - 1) if diff[i] * diff[i + 1] < 0]
+    zc = [times[i] + every * diff[i] / (diff[i] - diff[i + 1]) for i in range(len(diff) - 1)
+          if diff[i] * diff[i + 1] < 0]
     assert len(zc) >= 6
     period = 2 * float(np.mean(np.diff(zc)))
     print("ellipse nx %d: period %.0f (theory %d, paper model %d)" % (nx, period, theory, model))
