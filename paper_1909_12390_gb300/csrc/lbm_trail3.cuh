@@ -10,8 +10,8 @@
 //      plane k + LBM_T3_PREFETCH will read;
 //   2. collides and streams plane k of its range in place (psi(t) of the 18 neighbours from
 //      the current buffer, read-only in this launch), then arrives on the plane's mbarrier;
-//   3. (one thread) publishes, with st.release.gpu, the last plane that all of its threads have
-//      collided (mbarrier phases it finds complete);
+//   3. the warp whose arrival completes the plane's mbarrier phase publishes the plane (a
+//      release maximum on the CTA's progress flag);
 //   4. computes psi(t + 1) of plane p = k - LAG of its range into the other buffer: the
 //      densities of the state at t + 1 at a site are sums over slots written by the collisions
 //      of planes p - 1 .. p + 1 of this CTA and of the CTAs owning neighbour sites, so the
@@ -51,7 +51,7 @@ constexpr int kT3Threads = LBM_T3_THREADS;  // 14 warps, one site each of a 431-
 static_assert(kT3Threads % 32 == 0 && kT3Threads <= 1024, "trailing step block size");
 // planes between a plane's collision and its psi(t + 1) stage
 #ifndef LBM_T3_LAG
-#define LBM_T3_LAG 3
+#define LBM_T3_LAG 4
 #endif
 constexpr int kT3Lag = LBM_T3_LAG;
 static_assert(kT3Lag >= 2, "the psi stage of plane k - LAG needs plane k - LAG + 1 collided by the neighbours");
@@ -87,6 +87,10 @@ __device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity
       : "r"((unsigned)__cvta_generic_to_shared(b)), "r"(parity)
       : "memory");
   return r != 0;
+}
+// Monotone progress publication: flag = max(flag, v) with release semantics at GPU scope.
+__device__ __forceinline__ void atom_max_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 // L2 prefetch of the 16-byte units inside [lo, hi) (generic addresses of global memory): the
 // start is rounded up and the end down to 16 bytes, so the prefetch never leaves the range
@@ -204,14 +208,14 @@ __device__ __forceinline__ void trail3_body(const Params& P, typename Prec::S* _
     __syncwarp();  // orders the warp's later loads after the polling lanes' acquires
     ok = __all_sync(0xffffffffu, mine) && ok;
   };
-  int pub = -1;  // last plane published (thread 0)
-  auto publish = [&](int upto) {
-    bool adv = false;
-    while (pub < upto && mbar_test(&mbar[(pub + 1) % kT3Ring], (unsigned)(((pub + 1) / kT3Ring) & 1))) {
-      ++pub;
-      adv = true;
-    }
-    if (adv && b != A.silent_block) st_release_u64(&A.flags[b], base + (unsigned long long)pub + 1);
+  // After its arrival on plane z's mbarrier each warp checks whether the phase is complete;
+  // the warp whose arrival completed it (it sees the phase done, with every other thread's
+  // writes acquired) publishes z at once, as a monotone maximum, so the CTA's visible progress
+  // never lags its collisions.
+  auto arrive_publish = [&](int z) {
+    mbar_arrive(&mbar[z % kT3Ring]);
+    if ((tid & 31) == 0 && mbar_test(&mbar[z % kT3Ring], (unsigned)((z / kT3Ring) & 1)) && b != A.silent_block)
+      atom_max_release_u64(&A.flags[b], base + (unsigned long long)z + 1);
   };
 
   if (kT3Prefetch > 0 && tid == 0)
@@ -219,8 +223,7 @@ __device__ __forceinline__ void trail3_body(const Params& P, typename Prec::S* _
   for (int k = 0; k < nz; ++k) {
     if (kT3Prefetch > 0 && tid == 0 && k + kT3Prefetch < nz) prefetch(k + kT3Prefetch);
     collide(k);
-    mbar_arrive(&mbar[k % kT3Ring]);
-    if (tid == 0) publish(k);
+    arrive_publish(k);
     const int p = k - kT3Lag;
     if (p >= 1 && p <= nz - 2) {
       wait_cta(p + 1);
@@ -232,13 +235,6 @@ __device__ __forceinline__ void trail3_body(const Params& P, typename Prec::S* _
   // the planes whose stage needs the end of the march: nz - LAG .. nz - 1, and plane 0 (it
   // reads slots that plane nz - 1's collision writes)
   wait_cta(nz - 1);
-  if (tid == 0) {
-    unsigned it = 0;
-    while (pub < nz - 1 && ok) {
-      publish(nz - 1);
-      if (pub < nz - 1 && ++it > kSpinLimit) ok = false;
-    }
-  }
   wait_nbrs(nz - 1);
   ok = __all_sync(0xffffffffu, ok);
   if (ok) {
