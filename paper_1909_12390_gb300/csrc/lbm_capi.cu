@@ -80,7 +80,11 @@ struct lbm_ctx {
   std::vector<std::pair<int, int>> ev_marks[3];  // (start, stop) pool indices per kernel kind
   size_t ev_used = 0;
   // adjoint recording (lbm_record): checkpoints of the raw storage every ck_every steps
-  std::vector<void*> ckpt;
+  std::vector<void*> ckpt;  // pointers into ckpt_base, one per segment
+  void* ckpt_base = nullptr;
+  size_t ckpt_bytes = 0;
+  // captured step sequences of lbm_record's segments, by (steps, parity of the first step)
+  std::vector<std::pair<std::pair<int64_t, int>, cudaGraphExec_t>> seg_graphs;
   int ck_every = 0;
   int64_t rec_t0 = -1, rec_n = 0;
   std::string err;
@@ -116,8 +120,33 @@ lbm_status fail(lbm_ctx* c, lbm_status st, const char* fmt, ...) {
 }
 
 lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+  // a failed call leaves the runtime's last error set: clear it, so that a later call (of this
+  // or another context) does not report it as its own
+  cudaGetLastError();
   return fail(c, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "%s: %s", what,
               cudaGetErrorString(e));
+}
+
+// Host <-> device copies of caller arrays. A host range that straddles a page-locked registration
+// (part registered, part not) is refused by the copy itself with cudaErrorInvalidValue; such a
+// range goes through a pageable bounce buffer instead (the call synchronises the stream then).
+cudaError_t copy_in(void* dst, const void* src, size_t n, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s);
+  if (e != cudaErrorInvalidValue) return e;
+  cudaGetLastError();
+  std::vector<char> tmp((const char*)src, (const char*)src + n);
+  e = cudaMemcpyAsync(dst, tmp.data(), n, cudaMemcpyHostToDevice, s);
+  return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+}
+cudaError_t copy_out(void* dst, const void* src, size_t n, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s);
+  if (e != cudaErrorInvalidValue) return e;
+  cudaGetLastError();
+  std::vector<char> tmp(n);
+  e = cudaMemcpyAsync(tmp.data(), src, n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) std::memcpy(dst, tmp.data(), n);
+  return e;
 }
 
 #define CK(ctx, call)                                   \
@@ -295,6 +324,8 @@ void launch_steps(lbm_ctx* c, int64_t n, int64_t t0) {
 void drop_graph(lbm_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   c->graph = nullptr;
+  for (auto& g : c->seg_graphs) cudaGraphExecDestroy(g.second);
+  c->seg_graphs.clear();
 }
 
 void free_fused(lbm_ctx* c) {
@@ -548,6 +579,29 @@ bool build_graph(lbm_ctx* c) {
   return true;
 }
 
+// The captured graph of n steps starting at a step of the given parity (lbm_record's
+// segments), or nullptr when capture is not possible (the caller launches directly).
+cudaGraphExec_t segment_graph(lbm_ctx* c, int64_t n, int parity) {
+  for (auto& g : c->seg_graphs)
+    if (g.first.first == n && g.first.second == parity) return g.second;
+  if (c->graph_failed || c->stream == nullptr || c->seg_graphs.size() >= 8) return nullptr;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  launch_steps(c, n, parity);
+  cudaGraphExec_t x = nullptr;
+  if (cudaStreamEndCapture(c->stream, &g) != cudaSuccess || !g || cudaGraphInstantiate(&x, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    return nullptr;
+  }
+  cudaGraphDestroy(g);
+  c->seg_graphs.push_back({{n, parity}, x});
+  return x;
+}
+
 }  // namespace
 
 namespace lbm {
@@ -705,7 +759,7 @@ void lbm_destroy(lbm_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_graph(c);
   free_fused(c);
-  for (void* p : c->ckpt) cudaFree(p);
+  cudaFree(c->ckpt_base);
   cudaFree(c->f);
   cudaFree(c->psi);
   cudaFree(c->status);
@@ -766,12 +820,12 @@ lbm_status lbm_init(lbm_ctx* c, const double* rho, const double* u) {
   if (const double* m = mapped_range(rho, (size_t)c->nc * N))
     d_rho = const_cast<double*>(m);
   else
-    CK(c, cudaMemcpyAsync(d_rho, rho, (size_t)c->nc * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(c, copy_in(d_rho, rho, (size_t)c->nc * N * sizeof(double), c->stream));
   if (u) {
     if (const double* m = mapped_range(u, (size_t)3 * N))
       d_u = const_cast<double*>(m);
     else
-      CK(c, cudaMemcpyAsync(d_u, u, (size_t)3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      CK(c, copy_in(d_u, u, (size_t)3 * N * sizeof(double), c->stream));
   }
   // densities finite and > 0, u finite, and the component minima (the default FP32 shift)
   unsigned long long chk[6];
@@ -919,11 +973,10 @@ lbm_status lbm_fields(lbm_ctx* c, double* rho, double* u, double* p, double* psi
   c->ops->fields(c->P, c->f, c->psi, rho ? (m_rho ? m_rho : d_rho) : nullptr, u ? (m_u ? m_u : d_u) : nullptr,
                  p ? (m_p ? m_p : d_p) : nullptr, psi ? (m_psi ? m_psi : d_psi) : nullptr, parity, c->stream);
   CK(c, cudaGetLastError());
-  if (rho && !m_rho)
-    CK(c, cudaMemcpyAsync(rho, d_rho, (size_t)c->nc * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  if (u && !m_u) CK(c, cudaMemcpyAsync(u, d_u, (size_t)3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  if (p && !m_p) CK(c, cudaMemcpyAsync(p, d_p, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  if (psi && !m_psi) CK(c, cudaMemcpyAsync(psi, d_psi, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (rho && !m_rho) CK(c, copy_out(rho, d_rho, (size_t)c->nc * N * sizeof(double), c->stream));
+  if (u && !m_u) CK(c, copy_out(u, d_u, (size_t)3 * N * sizeof(double), c->stream));
+  if (p && !m_p) CK(c, copy_out(p, d_p, (size_t)N * sizeof(double), c->stream));
+  if (psi && !m_psi) CK(c, copy_out(psi, d_psi, (size_t)N * sizeof(double), c->stream));
   int64_t t = c->t;
   st = sync_status(c);
   c->t = t;
@@ -1034,22 +1087,48 @@ lbm_status lbm_record(lbm_ctx* c, int64_t n, int checkpoint_every) {
   if (c->P.split != LBM_SPLIT_VOLATILITY)
     return fail(c, LBM_ERR_ARG, "the adjoint covers the volatility split (Eq. distributionforce) only");
   if (n < 1 || checkpoint_every < 1) return fail(c, LBM_ERR_ARG, "n and checkpoint_every must be >= 1");
-  for (void* p : c->ckpt) cudaFree(p);
   c->ckpt.clear();
   c->rec_t0 = -1;
-  c->trail_t = -1;
   const size_t bytes = lbm_state_bytes(c);
   const int64_t t0 = c->t;
-  for (int64_t done = 0; done < n;) {
-    void* p = nullptr;
-    CK(c, cudaMalloc(&p, bytes));
+  const int64_t nseg = (n + checkpoint_every - 1) / checkpoint_every;
+  // one allocation for every checkpoint, kept for later recordings of the same size or less
+  const size_t need = (size_t)nseg * bytes;
+  if (c->ckpt_bytes < need) {
+    cudaFree(c->ckpt_base);
+    c->ckpt_base = nullptr;
+    c->ckpt_bytes = 0;
+    CK(c, cudaMalloc(&c->ckpt_base, need));
+    c->ckpt_bytes = need;
+  }
+  // the segments run back to back on the stream, each a captured graph of its steps (by step
+  // count and parity of its first step) after a copy of its starting state; the stream is
+  // synchronised once at the end. The trailing step keeps psi between steps and is driven
+  // through lbm_step instead.
+  const bool trailing = c->fused && c->fargs.mode == 4;
+  for (int64_t done = 0, i = 0; done < n; ++i) {
+    void* p = (char*)c->ckpt_base + (size_t)i * bytes;
     c->ckpt.push_back(p);
     CK(c, cudaMemcpyAsync(p, c->f, bytes, cudaMemcpyDeviceToDevice, c->stream));
     const int64_t k = std::min<int64_t>(checkpoint_every, n - done);
-    lbm_status st = lbm_step(c, k);
-    if (st != LBM_OK) return st;
+    if (trailing) {
+      lbm_status st = lbm_step(c, k);
+      if (st != LBM_OK) return st;
+    } else {
+      cudaGraphExec_t g = c->profiling ? nullptr : segment_graph(c, k, (int)((t0 + done) & 1));
+      if (g)
+        CK(c, cudaGraphLaunch(g, c->stream));
+      else
+        launch_steps(c, k, t0 + done);
+    }
     done += k;
   }
+  if (!trailing) {
+    CK(c, cudaGetLastError());
+    lbm_status st = sync_status(c);
+    if (st != LBM_OK) return st;
+  }
+  c->trail_t = -1;
   c->ck_every = checkpoint_every;
   c->rec_t0 = t0;
   c->rec_n = n;

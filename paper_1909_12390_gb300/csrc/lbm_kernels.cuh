@@ -683,7 +683,7 @@ __device__ __forceinline__ void psi_body(const Params& P, const typename Prec::S
 }
 
 template <int Q, int NC, class Prec>
-__global__ void __launch_bounds__(kBlock) k_psi(const Params P, const typename Prec::S* __restrict__ f,
+__global__ void __launch_bounds__(kBlock) k_psi(const __grid_constant__ Params P, const typename Prec::S* __restrict__ f,
                                                 typename Prec::PsiT* __restrict__ psi, int* status,
                                                 int parity) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -696,11 +696,6 @@ __global__ void __launch_bounds__(kBlock) k_psi(const Params P, const typename P
 }
 
 // Pass 2: S4-S6 of every site; psi of the neighbours from global memory.
-// LBM_COLLIDE_NOINLINE = 1 keeps one site's collision out of line: the kernel's own state
-// does not stay live across it, which leaves its registers to the collision (fewer spills).
-#ifndef LBM_COLLIDE_NOINLINE
-#define LBM_COLLIDE_NOINLINE 0
-#endif
 template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1>
 __device__ __forceinline__ void collide_site(const Params& P, typename Prec::S* __restrict__ f,
                                              const typename Prec::PsiT* __restrict__ psi, int x, int y, int z,
@@ -715,36 +710,15 @@ __device__ __forceinline__ void collide_site(const Params& P, typename Prec::S* 
   for (int a = 1; a < Q; ++a) pn[a] = (R)psi[s.nb(P, L::e(a, 0), L::e(a, 1), L::e(a, 2))];
   site_collide<Q, NC, Prec, MRT, PAR, GLOBAL>(P, f, s, pn, fo);
 }
-template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1>
-__device__ __attribute__((noinline)) void collide_site_noinline(const Params& P, typename Prec::S* __restrict__ f,
-                                                                 const typename Prec::PsiT* __restrict__ psi, int x,
-                                                                 int y, int z, typename Prec::S* fo) {
-  collide_site<Q, NC, Prec, MRT, PAR, GLOBAL>(P, f, psi, x, y, z, fo);
-}
-// S1-S3 of one site into psi_out[site]; returns the status bits (0 when fine).
-template <int Q, int NC, class Prec, int PAR>
-__device__ __attribute__((noinline)) int psi_site_noinline(const Params& P, const typename Prec::S* __restrict__ f,
-                                                            typename Prec::PsiT* __restrict__ psi_out, int x, int y,
-                                                            int z) {
-  Site s;
-  s.set_xyz(P, x, y, z);
-  typename Prec::PsiT v;
-  const int e = site_psi<Q, NC, Prec, PAR>(P, f, s, v);
-  psi_out[s.idx] = v;
-  return e;
-}
 template <int Q, int NC, class Prec, int MRT, int PAR>
 __device__ __forceinline__ void collide_body(const Params& P, typename Prec::S* __restrict__ f,
                                              const typename Prec::PsiT* __restrict__ psi, int x,
                                              typename Prec::S* fo = nullptr) {
-  if constexpr (LBM_COLLIDE_NOINLINE)
-    collide_site_noinline<Q, NC, Prec, MRT, PAR>(P, f, psi, x, blockIdx.y, blockIdx.z, fo);
-  else
-    collide_site<Q, NC, Prec, MRT, PAR>(P, f, psi, x, blockIdx.y, blockIdx.z, fo);
+  collide_site<Q, NC, Prec, MRT, PAR>(P, f, psi, x, blockIdx.y, blockIdx.z, fo);
 }
 
 template <int Q, int NC, class Prec, int MRT>
-__global__ void __launch_bounds__(kCollideThreads, kCollideBlocks) k_collide(const Params P, typename Prec::S* __restrict__ f,
+__global__ void __launch_bounds__(kCollideThreads, kCollideBlocks) k_collide(const __grid_constant__ Params P, typename Prec::S* __restrict__ f,
                                                        const typename Prec::PsiT* __restrict__ psi,
                                                        const int* status, long long* t_dev, int parity) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -763,7 +737,7 @@ __global__ void __launch_bounds__(kCollideThreads, kCollideBlocks) k_collide(con
 // the same slots, so fout needs no copy of fin first).
 template <int Q, int NC, class Prec, int MRT>
 __global__ void __launch_bounds__(kCollideThreads, kCollideBlocks)
-    k_collide_oop(const Params P, typename Prec::S* __restrict__ fin, typename Prec::S* __restrict__ fout,
+    k_collide_oop(const __grid_constant__ Params P, typename Prec::S* __restrict__ fin, typename Prec::S* __restrict__ fout,
                   const typename Prec::PsiT* __restrict__ psi, const int* status, long long* t_dev, int parity) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= P.nx) return;

@@ -6,13 +6,11 @@
 // pass before the first step), so the collisions of step t wait for nothing. CTA b owns the
 // contiguous range [range[b], range[b+1]) of the flattened (y, x) index of a z plane and
 // marches z = 0 .. nz-1; iteration k
-//   1. (one thread) prefetches into L2, with bulk prefetches, the slots that the collision of
-//      plane k + LBM_T3_PREFETCH will read;
-//   2. collides and streams plane k of its range in place (psi(t) of the 18 neighbours from
+//   1. collides and streams plane k of its range in place (psi(t) of the 18 neighbours from
 //      the current buffer, read-only in this launch), then arrives on the plane's mbarrier;
-//   3. the warp whose arrival completes the plane's mbarrier phase publishes the plane (a
+//   2. the warp whose arrival completes the plane's mbarrier phase publishes the plane (a
 //      release maximum on the CTA's progress flag);
-//   4. computes psi(t + 1) of plane p = k - LAG of its range into the other buffer: the
+//   3. computes psi(t + 1) of plane p = k - LAG of its range into the other buffer: the
 //      densities of the state at t + 1 at a site are sums over slots written by the collisions
 //      of planes p - 1 .. p + 1 of this CTA and of the CTAs owning neighbour sites, so the
 //      stage first waits (bounded) for its own CTA's mbarrier of plane p + 1 and for the
@@ -55,11 +53,6 @@ static_assert(kT3Threads % 32 == 0 && kT3Threads <= 1024, "trailing step block s
 #endif
 constexpr int kT3Lag = LBM_T3_LAG;
 static_assert(kT3Lag >= 2, "the psi stage of plane k - LAG needs plane k - LAG + 1 collided by the neighbours");
-// planes ahead of the collision that are prefetched into L2 (0: none)
-#ifndef LBM_T3_PREFETCH
-#define LBM_T3_PREFETCH 0
-#endif
-constexpr int kT3Prefetch = LBM_T3_PREFETCH;
 // population stores: 1 evict-first (st.global.cs), 2 write-back (st.global.wb, kept in L2 for the
 // psi stage)
 #ifndef LBM_T3_CS
@@ -92,43 +85,6 @@ __device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity
 __device__ __forceinline__ void atom_max_release_u64(unsigned long long* p, unsigned long long v) {
   asm volatile("red.release.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-// L2 prefetch of the 16-byte units inside [lo, hi) (generic addresses of global memory): the
-// start is rounded up and the end down to 16 bytes, so the prefetch never leaves the range
-__device__ __forceinline__ void bulk_prefetch_l2(const void* lo, const void* hi) {
-  const unsigned long long a = ((unsigned long long)lo + 15) & ~15ull, e = (unsigned long long)hi & ~15ull;
-  if (e <= a) return;
-  asm volatile(
-      "{\n\t.reg .u64 g;\n\tcvta.to.global.u64 g, %0;\n\tcp.async.bulk.prefetch.L2.global [g], %1;\n\t}" ::"l"(a),
-      "r"((unsigned)(e - a))
-      : "memory");
-}
-
-// L2 prefetch of the slots the collision of plane z of sites [r0, r0 + S) reads: at even steps
-// the range's own slots; at odd steps slot (x + e_b, b) for array b, i.e. plane z + e_b,z and the
-// range widened by one row and one site on each side. Out of line: its 57 address streams would
-// otherwise hold registers across the whole march.
-template <int NC, class Prec, int PAR>
-__device__ __attribute__((noinline)) void trail3_prefetch(const Params& P, const typename Prec::S* f, int r0, int S,
-                                                           int z) {
-  constexpr int Q = 19;
-  using L = Lat<Q>;
-  using S_ = typename Prec::S;
-  const int nx = P.nx, nz = P.nz, nxy = P.nx * P.ny;
-  const int lo = PAR ? r0 - nx - 1 : r0, hi = PAR ? r0 + S + nx + 1 : r0 + S;
-  const int lc = lo < 0 ? 0 : lo, hc = hi > nxy ? nxy : hi;
-#pragma unroll 1
-  for (int C = 0; C < NC; ++C) {
-    const S_* fc = f + (size_t)C * Q * P.N;
-#pragma unroll 1
-    for (int B = 0; B < Q; ++B) {
-      int zz = z + (PAR ? L::e(B, 2) : 0);
-      zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
-      const S_* p0 = fc + (size_t)B * P.N + (size_t)zz * nxy;
-      bulk_prefetch_l2(p0 + lc, p0 + hc);
-    }
-  }
-}
-
 template <int NC, class Prec, int MRT, int PAR>
 __device__ __forceinline__ void trail3_body(const Params& P, typename Prec::S* __restrict__ f, int* status,
                                             long long* t_dev, const FusedArgs& A, unsigned long long t) {
@@ -162,21 +118,24 @@ __device__ __forceinline__ void trail3_body(const Params& P, typename Prec::S* _
 
   int err = 0;
   bool ok = true;
-  auto prefetch = [&](int z) { trail3_prefetch<NC, Prec, PAR>(P, f, r0, S, z); };
   // the per-site work is out of line: the march's own state then does not stay live across the
   // collision's registers (the collision spills 8-24 bytes per site instead of several hundred)
   auto collide = [&](int z) {
 #pragma unroll 1
     for (int i = tid; i < S; i += kT3Threads) {
       const int xy = r0 + i;
-      collide_site_noinline<Q, NC, Prec, MRT, PAR, LBM_T3_CS>(P, f, psi_cur, xy % nx, xy / nx, z, nullptr);
+      collide_site<Q, NC, Prec, MRT, PAR, LBM_T3_CS>(P, f, psi_cur, xy % nx, xy / nx, z, nullptr);
     }
   };
   auto stage = [&](int z) {
 #pragma unroll 1
     for (int i = tid; i < S; i += kT3Threads) {
       const int xy = r0 + i;
-      err |= psi_site_noinline<Q, NC, Prec, 1 - PAR>(P, f, psi_next, xy % nx, xy / nx, z);
+      Site st;
+      st.set_xyz(P, xy % nx, xy / nx, z);
+      PsiT v;
+      err |= site_psi<Q, NC, Prec, 1 - PAR>(P, f, st, v);
+      psi_next[st.idx] = v;
     }
   };
   // this CTA's collisions of plane z (and of every plane before it) are complete
@@ -218,10 +177,7 @@ __device__ __forceinline__ void trail3_body(const Params& P, typename Prec::S* _
       atom_max_release_u64(&A.flags[b], base + (unsigned long long)z + 1);
   };
 
-  if (kT3Prefetch > 0 && tid == 0)
-    for (int z = 0; z < kT3Prefetch && z < nz; ++z) prefetch(z);
   for (int k = 0; k < nz; ++k) {
-    if (kT3Prefetch > 0 && tid == 0 && k + kT3Prefetch < nz) prefetch(k + kT3Prefetch);
     collide(k);
     arrive_publish(k);
     const int p = k - kT3Lag;
@@ -263,7 +219,8 @@ __device__ __forceinline__ void trail3_body(const Params& P, typename Prec::S* _
 
 template <int NC, class Prec, int MRT>
 __global__ void __maxnreg__(LBM_T3_MAXREG)
-    k_trail3(const Params P, typename Prec::S* __restrict__ f, int* status, long long* t_dev, const FusedArgs A) {
+    k_trail3(const __grid_constant__ Params P, typename Prec::S* __restrict__ f, int* status, long long* t_dev,
+             const __grid_constant__ FusedArgs A) {
   if (*(volatile int*)status) return;  // a previous step failed: do nothing
   const unsigned long long t = (unsigned long long)*(volatile long long*)t_dev;
   if (t & 1)
