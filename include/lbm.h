@@ -237,6 +237,20 @@ lbm_status lbm_profile_read(lbm_ctx *ctx, int kernel, double *total_ms, int64_t 
  * (FP32 for LBM_FP32_SHIFTED) with the EOS derivative and the reductions in FP64. Device
  * memory: checkpoint_every states plus four adjoint fields, allocated for the call. */
 lbm_status lbm_record(lbm_ctx *ctx, int64_t n, int checkpoint_every);
+/* Device memory of lbm_adjoint's reverse sweep. snapshots = 0 (the default) or >=
+ * checkpoint_every: each recorded segment's states are recomputed once and all kept
+ * (checkpoint_every state slots). 0 < snapshots < checkpoint_every: revolve-style binomial
+ * checkpointing inside each segment (Griewank's schedule): with s free slots the reversal of n
+ * steps advances m of them into a slot, reverses the last n - m with s - 1 slots, then the first
+ * m with s, m chosen so that no step is advanced more than r times, r the least integer with
+ * C(s + r, s) >= n. snapshots + 2 state slots are allocated; the gradients equal those of the
+ * full schedule bit for bit (the recomputed states are identical), at the cost of up to r
+ * recomputations per step. */
+lbm_status lbm_set_adjoint_memory(lbm_ctx *ctx, int snapshots);
+/* Forward steps the reverse sweep recomputes for one segment of n steps with the given state
+ * slots (0 or >= n: n - 1, every state once); host arithmetic only, no device. -1 for n < 1 or
+ * snapshots < 0. */
+int64_t lbm_revolve_steps(int64_t n, int snapshots);
 lbm_status lbm_adjoint(lbm_ctx *ctx, const double *drho, double *dkij, double *dgamma, double *drho0);
 
 /* ---- Batched lattices -------------------------------------------------------------------

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -86,6 +87,7 @@ struct lbm_ctx {
   // captured step sequences of lbm_record's segments, by (steps, parity of the first step)
   std::vector<std::pair<std::pair<int64_t, int>, cudaGraphExec_t>> seg_graphs;
   int ck_every = 0;
+  int adj_snaps = 0;  // lbm_adjoint: state slots per segment (0: every state of a segment)
   int64_t rec_t0 = -1, rec_n = 0;
   std::string err;
 };
@@ -1135,6 +1137,73 @@ lbm_status lbm_record(lbm_ctx* c, int64_t n, int checkpoint_every) {
   return LBM_OK;
 }
 
+namespace {
+
+// beta(c, r) = C(c + r, c): the most steps that c state snapshots, the one holding the start
+// included, reverse with every step advanced at most r times (binomial checkpointing;
+// saturates at 2^40). beta(c, r) = beta(c, r - 1) + beta(c - 1, r), beta(1, r) = r + 1.
+int64_t beta_cr(int c, int r) {
+  double b = 1.0;
+  for (int i = 1; i <= c; ++i) b = b * (double)(r + i) / (double)i;
+  return b > 1099511627776.0 ? (int64_t)1099511627776 : (int64_t)(b + 0.5);
+}
+// Fewest forward steps that reverse l steps with c snapshots (the start's included):
+// t(l, c) = r l - beta(c + 1, r - 1) for beta(c, r - 1) < l <= beta(c, r) (Griewank's binomial
+// checkpointing); t(l, 1) = l (l - 1) / 2.
+int64_t revolve_min(int64_t l, int c) {
+  if (l <= 1) return 0;
+  if (c <= 1) return l * (l - 1) / 2;
+  int r = 0;
+  while (beta_cr(c, r) < l) ++r;
+  return (int64_t)r * l - beta_cr(c + 1, r - 1);
+}
+// First advance of an optimal reversal of n >= 2 steps with s >= 1 free slots besides the one
+// holding the start (c = s + 1 snapshots): the m whose split attains the least total,
+// m + t(n - m, c - 1) + t(m, c) = t(n, c), searched over the binomial interval
+// [n - beta(c - 1, r), beta(c, r - 1)] (the right part reversible with c - 1 snapshots, the left
+// part with c snapshots and one repetition fewer), r the least with beta(c, r) >= n.
+int64_t binomial_split(int64_t n, int s) {
+  const int c = s + 1;
+  int r = 0;
+  while (beta_cr(c, r) < n) ++r;
+  int64_t lo = std::max<int64_t>(1, n - beta_cr(c - 1, r));
+  int64_t hi = std::min<int64_t>(n - 1, r > 0 ? beta_cr(c, r - 1) : 1);
+  if (hi < lo) hi = lo;
+  const int64_t best = revolve_min(n, c);
+  int64_t arg = lo, val = -1;
+  for (int64_t m = lo; m <= hi; ++m) {
+    const int64_t v = m + revolve_min(n - m, c - 1) + revolve_min(m, c);
+    if (v == best) return m;
+    if (val < 0 || v < val) {
+      val = v;
+      arg = m;
+    }
+  }
+  return arg;
+}
+
+}  // namespace
+
+int64_t revolve_count(int64_t n, int s) {
+  if (n <= 1) return 0;
+  if (s == 0) return n * (n - 1) / 2;
+  const int64_t m = binomial_split(n, s);
+  return m + revolve_count(n - m, s - 1) + revolve_count(m, s);
+}
+
+int64_t lbm_revolve_steps(int64_t n, int snapshots) {
+  if (n < 1 || snapshots < 0) return -1;
+  if (snapshots == 0 || snapshots >= n) return n - 1;
+  return revolve_count(n, snapshots);
+}
+
+lbm_status lbm_set_adjoint_memory(lbm_ctx* c, int snapshots) {
+  if (!c) return LBM_ERR_ARG;
+  if (snapshots < 0) return fail(c, LBM_ERR_ARG, "snapshots must be >= 0");
+  c->adj_snaps = snapshots;
+  return LBM_OK;
+}
+
 lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dgamma, double* drho0) {
   if (!c || !drho) return c ? fail(c, LBM_ERR_ARG, "drho is NULL") : LBM_ERR_ARG;
   if (c->rec_t0 < 0 || c->rec_t0 + c->rec_n != c->t)
@@ -1144,7 +1213,10 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
   const int nc = c->nc, Q = c->Q, K = c->ck_every;
   const size_t sbytes = lbm_state_bytes(c), lbytes = (size_t)nc * Q * N * A->real_bytes;
   const unsigned nblk = (unsigned)((N + A->block - 1) / A->block);  // blocks of pass A / B
-  std::vector<void*> snaps((size_t)K, nullptr);
+  // revolve-style reversal inside each segment with S state slots when S < K; otherwise every
+  // state of a segment is recomputed once and kept (K slots)
+  const int S = (c->adj_snaps > 0 && c->adj_snaps < K) ? c->adj_snaps : 0;
+  std::vector<void*> snaps((size_t)(S > 0 ? S + 2 : K), nullptr);
   void *la = nullptr, *lb = nullptr, *Fb = nullptr, *jb = nullptr, *rb = nullptr, *psis = nullptr;
   double *gpart = nullptr, *kpart = nullptr, *dd = nullptr;
   int* st_s = nullptr;
@@ -1156,7 +1228,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
   for (auto& p : snaps) alloc(&p, sbytes);
   // psi of every state of a segment, computed once by the replay and read by the reverse steps
   const size_t pbytes = (size_t)N * c->ops->psi_bytes;
-  alloc(&psis, (size_t)K * pbytes);
+  alloc(&psis, (size_t)(S > 0 ? 1 : K) * pbytes);
   auto psi_of = [&](int i) { return (void*)((char*)psis + (size_t)i * pbytes); };
   alloc(&la, lbytes);
   alloc(&lb, lbytes);
@@ -1202,6 +1274,56 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
     }
     return r;
   };
+  // Revolve-style reversal of steps [t0, t0 + n) from the state at t0 in `base`, with the free
+  // slots snaps[0 .. s) and the scratch buffers snaps[S], snaps[S + 1] (out-of-place steps
+  // alternate between them). One step back needs its state and psi: psi into psis, pass A, pass B.
+  // Recomputed states are bit-identical to the recorded ones, so the gradients equal those of
+  // the full-storage schedule bit for bit.
+  auto advance = [&](int64_t t0, const void* from, int64_t m, void* to) {
+    // m >= 1 out-of-place steps from `from` (state t0); the last lands in `to`
+    cudaError_t r = cudaSuccess;
+    const void* cur = from;
+    void* scratch[2] = {snaps[S], snaps[S + 1]};
+    for (int64_t i = 0; i < m && r == cudaSuccess; ++i) {
+      void* nxt = i == m - 1 ? to : scratch[(m - 1 - i) & 1];
+      const int parity = (int)((t0 + i) & 1);
+      c->ops->psi(c->P, cur, psis, st_s, parity, c->stream);
+      c->ops->collide_oop(c->P, cur, nxt, psis, st_s, t_s, parity, c->stream);
+      r = cudaGetLastError();
+      cur = nxt;
+    }
+    return r;
+  };
+  auto back_step = [&](int64_t t, const void* state) {
+    const int parity = (int)(t & 1);
+    c->ops->psi(c->P, state, psis, st_s, parity, c->stream);
+    A->pass_a(c->P, state, psis, la, Fb, jb, rb, parity, gpart, c->stream);
+    A->pass_b(c->P, state, psis, la, Fb, jb, rb, lb, parity, kpart, c->stream);
+    std::swap(la, lb);
+    return cudaGetLastError();
+  };
+  std::function<cudaError_t(int64_t, int64_t, const void*, int)> revolve = [&](int64_t t0, int64_t n,
+                                                                                const void* base, int s_) {
+    if (n == 1) return back_step(t0, base);
+    if (s_ == 0) {  // no slot left: recompute each state from the base, last first
+      cudaError_t r = cudaSuccess;
+      for (int64_t i = n - 1; i >= 0 && r == cudaSuccess; --i) {
+        if (i == 0) {
+          r = back_step(t0, base);
+        } else {
+          r = advance(t0, base, i, snaps[S]);
+          if (r == cudaSuccess) r = back_step(t0 + i, snaps[S]);
+        }
+      }
+      return r;
+    }
+    const int64_t m = binomial_split(n, s_);
+    void* slot = snaps[s_ - 1];
+    cudaError_t r = advance(t0, base, m, slot);
+    if (r == cudaSuccess) r = revolve(t0 + m, n - m, slot, s_ - 1);
+    if (r == cudaSuccess) r = revolve(t0, m, base, s_);
+    return r;
+  };
   // Full segments repeat one launch sequence, which is captured as a graph per (parity of t_k,
   // which buffer is la) and replayed; a failed capture falls back to direct launches.
   cudaGraphExec_t gx[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -1211,6 +1333,10 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
   for (int k = nseg - 1; k >= 0 && e == cudaSuccess; --k) {
     const int64_t tk = c->rec_t0 + (int64_t)k * K;
     const int len = (int)std::min<int64_t>(K, c->rec_t0 + c->rec_n - tk);
+    if (S > 0) {  // the recorded checkpoint is read, never written
+      e = revolve(tk, len, c->ckpt[k], S);
+      continue;
+    }
     e = cudaMemcpyAsync(snaps[0], c->ckpt[k], sbytes, cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) break;
     if (len == K && K > 1) {

@@ -28,7 +28,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_init", "lbm_step"
            "lbm_step_static", "lbm_step_static_error", "lbm_batch_create", "lbm_batch_destroy",
            "lbm_batch_init", "lbm_batch_step", "lbm_batch_case_status", "lbm_batch_fields",
            "lbm_batch_get_f", "lbm_batch_tune", "lbm_batch_tune_report", "lbm_batch_sites",
-           "lbm_batch_last_error", "lbm_record", "lbm_adjoint", "lbm_flash", "lbm_flash_error", "lbm_diagnostics")
+           "lbm_batch_last_error", "lbm_record", "lbm_adjoint", "lbm_set_adjoint_memory", "lbm_revolve_steps", "lbm_flash", "lbm_flash_error", "lbm_diagnostics")
 STATIC_MAX_SITES = 1048576
 PATH_AUTO, PATH_TWO_KERNEL, PATH_FUSED, PATH_TRAILING = 0, 1, 2, 3
 FUSED_TILES, FUSED_PLANES = 1, 3
@@ -148,6 +148,9 @@ def lib() -> ctypes.CDLL:
         L.lbm_batch_last_error.restype = ctypes.c_char_p
         L.lbm_record.argtypes = [vp, ctypes.c_int64, ctypes.c_int]
         L.lbm_adjoint.argtypes = [vp, _DP, _DP, _DP, _DP]
+        L.lbm_set_adjoint_memory.argtypes = [vp, ctypes.c_int]
+        L.lbm_revolve_steps.argtypes = [ctypes.c_int64, ctypes.c_int]
+        L.lbm_revolve_steps.restype = ctypes.c_int64
         L.lbm_last_error.argtypes = [vp]
         L.lbm_last_error.restype = ctypes.c_char_p
         L.lbm_scale_to_lattice.argtypes = [ctypes.c_int, ctypes.POINTER(Component), ctypes.c_double,
@@ -191,6 +194,12 @@ def make_args(shape, components, T, gamma=None, kij=None, beta=1.0, G=-1.0, coll
               gamma=arr(gamma, nc), beta=beta, G=G, collision=collision,
               mrt_rates=arr(mrt_rates, Q), precision=precision, rho_ref=arr(rho_ref, nc), split=int(split))
     return Grid(nx, ny, nz, Q), comps, eos, keep
+
+
+def revolve_steps(n: int, snapshots: int) -> int:
+    """lbm_revolve_steps: forward steps the adjoint's reverse sweep recomputes for a segment of
+    n steps with the given state slots."""
+    return int(lib().lbm_revolve_steps(int(n), int(snapshots)))
 
 
 def step_static(shape, components, T, tau, f_device_ptr: int, t0: int, n: int, stream: int = 0, **kw):
@@ -375,6 +384,11 @@ class Lattice:
     def record(self, n: int, checkpoint_every: int):
         """Advance n steps keeping checkpoints for lbm_adjoint."""
         self._check(lib().lbm_record(self._h, int(n), int(checkpoint_every)))
+
+    def set_adjoint_memory(self, snapshots: int):
+        """State slots of lbm_adjoint's reverse sweep per segment: 0 keeps every state of a
+        segment; fewer than checkpoint_every selects revolve-style binomial checkpointing."""
+        self._check(lib().lbm_set_adjoint_memory(self._h, int(snapshots)))
 
     def adjoint(self, drho):
         """Back-propagate dL/drho(final) (array (nc, *grid)) through the recorded steps.
