@@ -114,56 +114,21 @@ __device__ __forceinline__ int site_psi_dl(const Params& P, const typename Prec:
   return 0;
 }
 
-// Order in which a site's populations are summed into its density, the same on every path:
-// grouped by the direction's component along the slowest axis (z in 3-D, y in 2-D),
-//   rho_s = (G_up + G_mid) + G_down,  G_up = sum over e_last = +1, G_mid over e_last = 0,
-//   G_down over e_last = -1, each group summed left to right in ascending direction index.
-// After a step f_a(x) = f*_a(x - e_a), so G_up of a site holds values collided on the plane
-// below it, G_mid on its own plane and G_down on the plane above: a step that marches the
-// slowest axis can form the next step's densities from the values it has just written, in
-// this same order (bit for bit what a separate pass over the stored values computes).
-template <int Q>
-struct DensOrder {
-  static constexpr int D = Lat<Q>::D;
-  __host__ __device__ static constexpr int grp(int a) { return Lat<Q>::e(a, D - 1); }
-  // k-th direction of group g (+1, 0, -1) in ascending index, -1 past its end
-  __host__ __device__ static constexpr int dir(int g, int k) {
-    for (int a = 0; a < Q; ++a)
-      if (grp(a) == g && k-- == 0) return a;
-    return -1;
-  }
-  __host__ __device__ static constexpr int count(int g) {
-    int n = 0;
-    for (int a = 0; a < Q; ++a) n += grp(a) == g ? 1 : 0;
-    return n;
-  }
-};
-
-// Sum of the populations of group g at site s, in the order above; V(a) returns f_a.
-template <int Q, int G, class R, class V>
-__device__ __forceinline__ R dens_group(V&& v) {
-  using DO = DensOrder<Q>;
-  R acc = v(std::integral_constant<int, DO::dir(G, 0)>{});
-  For<1, DO::count(G)>::run([&]<int K>() { acc += v(std::integral_constant<int, DO::dir(G, K)>{}); });
-  return acc;
-}
-template <int Q, class R, class V>
-__device__ __forceinline__ R dens_sum(V&& v) {
-  const R up = dens_group<Q, 1, R>(v);
-  const R mid = dens_group<Q, 0, R>(v);
-  const R down = dens_group<Q, -1, R>(v);
-  return (up + mid) + down;
-}
-
-// Shifted densities of one site, summed in the order of DensOrder (as site_moments does), so
-// that every path computes bit-identical densities.
+// Shifted densities of one site, summed in the same order as site_moments (rest, then the
+// pairs), so that every path computes bit-identical densities.
 template <int Q, int NC, class Prec, int PAR>
 __device__ __forceinline__ void site_densities(const Params& P, const typename Prec::S* __restrict__ f,
                                                const Site& s, typename Prec::R (&d)[NC]) {
   using R = typename Prec::R;
+  using L = Lat<Q>;
   For<0, NC>::run([&]<int C>() {
     const typename Prec::S* fc = comp_base<Q>(f, P, C);
-    d[C] = dens_sum<Q, R>([&](auto a_) { return (R)fc[AA<Q>::template rd<decltype(a_)::value, PAR>(P, s)]; });
+    R acc = (R)fc[AA<Q>::template rd<0, PAR>(P, s)];
+    For<0, L::NPAIR>::run([&]<int K>() {
+      constexpr int a = L::pfirst(K), b = L::opp(a);
+      acc += (R)fc[AA<Q>::template rd<a, PAR>(P, s)] + (R)fc[AA<Q>::template rd<b, PAR>(P, s)];
+    });
+    d[C] = acc;
   });
 }
 
@@ -228,50 +193,33 @@ __device__ __forceinline__ void gong_split(const Params& P, const R (&rc)[NC], R
   for (int i = 0; i < NC; ++i) chi[i] = (R)(w[i] / ws);
 }
 
-// S1 moments of one component c at one site: its shifted density dl_c = sum_a f_ca =
-// rho_c - rho_ref_c (in the order of DensOrder) and its momentum j_c = sum_a e_a f_ca, summed
-// from the differences of opposite populations: near equilibrium the two are close, so in FP32
-// each difference is exact and j carries no rounding on the scale of the populations.
-template <int Q, int C, class Prec, int PAR>
-__device__ __forceinline__ void comp_moments(const Params& P, const typename Prec::S* __restrict__ f, const Site& s,
-                                             typename Prec::R& dl, typename Prec::R (&jc)[3]) {
-  using R = typename Prec::R;
-  using L = Lat<Q>;
-  const typename Prec::S* fc = comp_base<Q>(f, P, C);
-  R v[Q];
-  For<0, Q>::run([&]<int A>() { v[A] = (R)fc[AA<Q>::template rd<A, PAR>(P, s)]; });
-  dl = dens_sum<Q, R>([&](auto a_) { return v[decltype(a_)::value]; });
-  jc[0] = jc[1] = jc[2] = 0;
-  For<0, L::NPAIR>::run([&]<int K>() {
-    constexpr int a = L::pfirst(K), b = L::opp(a);
-    const R d = v[a] - v[b];
-#pragma unroll
-    for (int k = 0; k < L::D; ++k) {
-      if (L::e(a, k) > 0) jc[k] += d;
-      if (L::e(a, k) < 0) jc[k] -= d;
-    }
-  });
-}
-
-// The site's total momentum from the components' momenta, summed in component order.
-template <int NC, class R>
-__device__ __forceinline__ void sum_momenta(const R (&jc)[NC][3], R (&j)[3]) {
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    j[k] = jc[0][k];
-#pragma unroll
-    for (int c = 1; c < NC; ++c) j[k] += jc[c][k];
-  }
-}
-
-// S1 moments of one site: the shifted densities of every component and the total momentum.
+// S1 moments of one site: shifted component densities dl_c = sum_a f_ca = rho_c - rho_ref_c
+// and the total momentum j = sum_c sum_a e_a f_ca. The momentum is summed from the differences
+// of opposite populations: near equilibrium the two are close, so in FP32 each difference is
+// exact and j carries no rounding on the scale of the populations.
 template <int Q, int NC, class Prec, int PAR>
 __device__ __forceinline__ void site_moments(const Params& P, const typename Prec::S* __restrict__ f, const Site& s,
                                              typename Prec::R (&dl)[NC], typename Prec::R (&j)[3]) {
   using R = typename Prec::R;
-  R jc[NC][3];
-  For<0, NC>::run([&]<int C>() { comp_moments<Q, C, Prec, PAR>(P, f, s, dl[C], jc[C]); });
-  sum_momenta<NC, R>(jc, j);
+  using L = Lat<Q>;
+  j[0] = j[1] = j[2] = 0;
+  For<0, NC>::run([&]<int C>() {
+    const typename Prec::S* fc = comp_base<Q>(f, P, C);
+    R acc = (R)fc[AA<Q>::template rd<0, PAR>(P, s)];
+    For<0, L::NPAIR>::run([&]<int K>() {
+      constexpr int a = L::pfirst(K), b = L::opp(a);
+      const R va = (R)fc[AA<Q>::template rd<a, PAR>(P, s)];
+      const R vb = (R)fc[AA<Q>::template rd<b, PAR>(P, s)];
+      acc += va + vb;
+      const R d = va - vb;
+#pragma unroll
+      for (int k = 0; k < L::D; ++k) {
+        if (L::e(a, k) > 0) j[k] += d;
+        if (L::e(a, k) < 0) j[k] -= d;
+      }
+    });
+    dl[C] = acc;
+  });
 }
 
 // The two members of a pair of opposite populations pass through identical arithmetic. In
