@@ -58,12 +58,12 @@ def peaks():
 
 
 def kernel_source_sha():
-    """Hash of what defines the benchmarked kernels (k_psi, k_collide, k_fused3 of the D3Q19
-    FP32-shifted MRT unit): their headers, the unit and the build flags."""
+    """Hash of what defines the benchmarked kernels (k_psi, k_collide, k_fused3, k_trail3 of the
+    D3Q19 FP32-shifted MRT unit): their headers, the unit and the build flags."""
     h = hashlib.sha256()
     pkg = os.path.join(ROOT, "paper_1909_12390_gb300")
-    files = [os.path.join("csrc", f) for f in ("lbm_core.cuh", "lbm_kernels.cuh", "lbm_fused3.cuh", "lbm_ops.h",
-                                               "lbm_d3q19_f32s_mrt.cu")] + ["build.py"]
+    files = [os.path.join("csrc", f) for f in ("lbm_core.cuh", "lbm_kernels.cuh", "lbm_fused3.cuh", "lbm_trail3.cuh",
+                                               "lbm_ops.h", "lbm_d3q19_f32s_mrt.cu")] + ["build.py"]
     for fn in files:
         with open(os.path.join(pkg, fn), "rb") as fh:
             h.update(fn.encode() + fh.read())
@@ -579,6 +579,8 @@ def main():
                     help="skip the per-workload error check against the stored oracle runs")
     ap.add_argument("--grid", type=int, default=0,
                     help="cube edge of a smaller case of the same workload (profiling); 0 = 256")
+    ap.add_argument("--fp64", action="store_true",
+                    help="time FP64 storage instead of FP32-shifted (profiling the FP64 path)")
     ap.add_argument("--nz", type=int, default=0,
                     help="z extent of a shorter case with the same planes (profiling); 0 = cube")
     args = ap.parse_args()
@@ -614,7 +616,7 @@ def main():
     N = int(np.prod(c["shape"]))
     rho0 = init_fields(c)
 
-    gpu = lattice_for(c, lbm.FP32_SHIFTED)
+    gpu = lattice_for(c, lbm.FP64 if args.fp64 else lbm.FP32_SHIFTED)
     if args.path != "auto":
         gpu.set_path({"fused": lbm.PATH_FUSED, "two": lbm.PATH_TWO_KERNEL, "trailing": lbm.PATH_TRAILING}[args.path])
     gpu.init(rho0)
@@ -657,7 +659,7 @@ def main():
     # FP32 population, 2 * 19 * nc * 4 B per site (the fused kernel and the collide pass each
     # move exactly that; psi traffic is not counted)
     peak, peak_kind = peaks()
-    alg_site = 2 * 19 * nc * 4
+    alg_site = 2 * 19 * nc * (8 if args.fp64 else 4)
     if path == lbm.PATH_TRAILING:
         kname, kavg = "k_trail3", fus_ms / max(fus_n, 1)
         kinds = {kname: kavg}
