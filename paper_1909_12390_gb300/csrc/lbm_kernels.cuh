@@ -643,6 +643,81 @@ __global__ void __launch_bounds__(kBlock) k_psi(const __grid_constant__ Params P
     psi_body<Q, NC, Prec, 0>(P, f, psi, status, x);
 }
 
+// LBM_PSI_VEC4 = 1: the FP32-shifted pseudo-potential pass with 128-bit loads, four consecutive
+// x sites per thread (nx divisible by 4). A slot run of four sites starts on a 16-byte boundary
+// for every direction at even steps and for the directions without an x component at odd steps
+// (one float4 load each); the x-shifted runs of odd steps are loaded site by site. Each site's
+// densities are summed in site_densities' order, so psi is bit-identical to k_psi's.
+#ifndef LBM_PSI_VEC4
+#define LBM_PSI_VEC4 0
+#endif
+template <int Q, int NC, class Prec, int PAR>
+__device__ __forceinline__ void psi4_body(const Params& P, const float* __restrict__ f, float* __restrict__ psi,
+                                          int* status, int x4) {
+  using L = Lat<Q>;
+  Site s;
+  s.set_xyz(P, x4, blockIdx.y, blockIdx.z);
+  float d[4][NC];
+  For<0, NC>::run([&]<int C>() {
+    const float* fc = comp_base<Q>(f, P, C);
+    float v[Q][4];
+    For<0, Q>::run([&]<int A>() {
+      constexpr int ex = L::e(A, 0);
+      if constexpr (PAR == 0 || ex == 0) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(fc + AA<Q>::template rd<A, PAR>(P, s)));
+        v[A][0] = q.x;
+        v[A][1] = q.y;
+        v[A][2] = q.z;
+        v[A][3] = q.w;
+      } else {
+        // slot (x - e_a, opp a): the run x4 - ex .. x4 + 3 - ex of the row, wrapped at its ends
+        constexpr int O = L::opp(A);
+        const uint32_t row = s.nb(P, 0, -L::e(A, 1), -L::e(A, 2)) - (uint32_t)x4;
+        const float* r = fc + (size_t)O * P.N + row;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          int xx = x4 + k - ex;
+          xx = xx < 0 ? xx + P.nx : (xx >= P.nx ? xx - P.nx : xx);
+          v[A][k] = __ldg(r + xx);
+        }
+      }
+    });
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float acc = v[0][k];
+      For<0, L::NPAIR>::run([&]<int K>() {
+        constexpr int a = L::pfirst(K), b = L::opp(a);
+        acc += v[a][k] + v[b][k];
+      });
+      d[k][C] = acc;
+    }
+  });
+  float out[4];
+  int err = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float pv;
+    err |= site_psi_dl<NC, Prec>(P, d[k], pv);
+    out[k] = pv;
+  }
+  if (err) {
+    atomicOr(status, err);
+    return;
+  }
+  *reinterpret_cast<float4*>(psi + s.idx) = make_float4(out[0], out[1], out[2], out[3]);
+}
+template <int Q, int NC, class Prec>
+__global__ void __launch_bounds__(kBlock) k_psi4(const __grid_constant__ Params P, const float* __restrict__ f,
+                                                 float* __restrict__ psi, int* status, int parity) {
+  const int x4 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (x4 >= P.nx) return;
+  if (*(volatile int*)status) return;
+  if (parity)
+    psi4_body<Q, NC, Prec, 1>(P, f, psi, status, x4);
+  else
+    psi4_body<Q, NC, Prec, 0>(P, f, psi, status, x4);
+}
+
 // Pass 2: S4-S6 of every site; psi of the neighbours from global memory.
 template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1>
 __device__ __forceinline__ void collide_site(const Params& P, typename Prec::S* __restrict__ f,
@@ -665,15 +740,63 @@ __device__ __forceinline__ void collide_body(const Params& P, typename Prec::S* 
   collide_site<Q, NC, Prec, MRT, PAR>(P, f, psi, x, blockIdx.y, blockIdx.z, fo);
 }
 
+// LBM_COLLIDE_PSI_SMEM = 1: the block first stages the pseudo-potential its sites' stencils
+// need in shared memory (the rows (y + dy, z + dz) around its row segment, one site of halo at
+// each x end, coalesced loads), then every site reads its 19 values from there; 0 (the default,
+// faster on GB300, see the design notes): each site loads them from global memory (L1 / L2).
+#ifndef LBM_COLLIDE_PSI_SMEM
+#define LBM_COLLIDE_PSI_SMEM 0
+#endif
+template <int Q, int NC, class Prec, int MRT, int PAR>
+__device__ __forceinline__ void collide_body_smem(const Params& P, typename Prec::S* __restrict__ f,
+                                                  const typename Prec::PsiT* __restrict__ psi) {
+  using R = typename Prec::R;
+  using PsiT = typename Prec::PsiT;
+  using L = Lat<Q>;
+  constexpr int NR = Q == 19 ? 9 : 3;  // rows (dy, dz) of the stencil
+  __shared__ PsiT sp[NR][kCollideThreads + 2];
+  const int bx = blockDim.x, x0 = blockIdx.x * bx, y = blockIdx.y, z = blockIdx.z;
+  const int w = min(bx, P.nx - x0) + 2;
+  for (int r = 0; r < NR; ++r) {
+    const int dy = r / 3 - 1, dz = Q == 19 ? r % 3 - 1 : 0;
+    const int yy = dy == 0 ? y : (dy > 0 ? (y == P.ny - 1 ? 0 : y + 1) : (y == 0 ? P.ny - 1 : y - 1));
+    const int zz = dz == 0 ? z : (dz > 0 ? (z == P.nz - 1 ? 0 : z + 1) : (z == 0 ? P.nz - 1 : z - 1));
+    const PsiT* row = psi + ((size_t)zz * P.ny + yy) * P.nx;
+    for (int i = threadIdx.x; i < w; i += bx) {
+      int xx = x0 - 1 + i;
+      xx = xx < 0 ? xx + P.nx : (xx >= P.nx ? xx - P.nx : xx);
+      sp[r][i] = row[xx];
+    }
+  }
+  __syncthreads();
+  const int x = x0 + threadIdx.x;
+  if (x >= P.nx) return;
+  R pn[Q];
+  For<0, Q>::run([&]<int A>() {
+    constexpr int r = (L::e(A, 1) + 1) * 3 + (Q == 19 ? L::e(A, 2) + 1 : 0);
+    pn[A] = (R)sp[Q == 19 ? r : L::e(A, 1) + 1][threadIdx.x + 1 + L::e(A, 0)];
+  });
+  Site s;
+  s.set_xyz(P, x, y, z);
+  site_collide<Q, NC, Prec, MRT, PAR>(P, f, s, pn);
+}
+
 template <int Q, int NC, class Prec, int MRT>
 __global__ void __launch_bounds__(kCollideThreads, kCollideBlocks) k_collide(const __grid_constant__ Params P, typename Prec::S* __restrict__ f,
                                                        const typename Prec::PsiT* __restrict__ psi,
                                                        const int* status, long long* t_dev, int parity) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= P.nx) return;
   if (*(volatile const int*)status) return;
   // the step counter advances only for steps whose pseudo-potential pass succeeded
   if (x == 0 && blockIdx.y == 0 && blockIdx.z == 0) *t_dev += 1;
+  if constexpr (LBM_COLLIDE_PSI_SMEM) {
+    if (parity)
+      collide_body_smem<Q, NC, Prec, MRT, 1>(P, f, psi);
+    else
+      collide_body_smem<Q, NC, Prec, MRT, 0>(P, f, psi);
+    return;
+  }
+  if (x >= P.nx) return;
   if (parity)
     collide_body<Q, NC, Prec, MRT, 1>(P, f, psi, x);
   else
@@ -1169,6 +1292,15 @@ struct Launch {
     grid = dim3((unsigned)((P.nx + tx - 1) / tx), (unsigned)P.ny, (unsigned)P.nz);
   }
   static void psi(const Params& P, const void* f, void* ps, int* st, int parity, cudaStream_t s) {
+    if constexpr (LBM_PSI_VEC4 && std::is_same_v<S, float>) {
+      if (P.nx % 4 == 0) {
+        int tx = 32;
+        while (tx < P.nx / 4 && tx < kBlock) tx *= 2;
+        const dim3 g((unsigned)((P.nx / 4 + tx - 1) / tx), (unsigned)P.ny, (unsigned)P.nz);
+        k_psi4<Q, NC, Prec><<<g, tx, 0, s>>>(P, (const float*)f, (float*)ps, st, parity);
+        return;
+      }
+    }
     dim3 g, b;
     site_grid(P, g, b);
     k_psi<Q, NC, Prec><<<g, b, 0, s>>>(P, (const S*)f, (PsiT*)ps, st, parity);
