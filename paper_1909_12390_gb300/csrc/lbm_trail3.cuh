@@ -99,7 +99,7 @@ __device__ __forceinline__ void trail3_body(const Params& P, typename Prec::S* _
 
   const int tid = threadIdx.x, b = blockIdx.x;
   const int r0 = A.range[b], S = A.range[b + 1] - r0;
-  const int nx = P.nx, nz = P.nz, nxy = P.nx * P.ny;
+  const int nx = P.nx, nz = P.nz;
   // progress value: planes collided + 1, at most nz + 1 in a launch
   const unsigned long long base = t * (unsigned long long)(nz + 2);
   const PsiT* __restrict__ psi_cur = (const PsiT*)A.psi_ring + (size_t)(t & 1) * P.N;
