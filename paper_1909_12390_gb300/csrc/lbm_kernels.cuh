@@ -39,8 +39,17 @@ constexpr int kBlock = 256;
 #ifndef LBM_COLLIDE_BLOCKS
 #define LBM_COLLIDE_BLOCKS 4
 #endif
+// The D3Q19 FP64 collision is bound by GB300's FP64 pipe rather than by latency, so it trades
+// resident warps for registers: at 2 blocks (up to 255 registers) it spills 56 B per thread
+// instead of about 2 KB, and measured 37.21 ms per 256^3 collide pass against 37.50 ms at 4
+// (3 blocks: 37.63 ms).
+#ifndef LBM_COLLIDE_BLOCKS_F64
+#define LBM_COLLIDE_BLOCKS_F64 2
+#endif
 constexpr int kCollideThreads = LBM_COLLIDE_THREADS;
 constexpr int kCollideBlocks = LBM_COLLIDE_BLOCKS;
+template <int Q, class Prec>
+constexpr int kCollideBlocksOf = Q == 19 && sizeof(typename Prec::R) == 8 ? LBM_COLLIDE_BLOCKS_F64 : kCollideBlocks;
 // Per-pair values of a site shared by every component and both passes of the collision
 // (w Pe, 3 w e.u, Fe, Fo): 1 computes them once per site and holds them in registers, 0
 // recomputes them in each pass. At 256^3 (D3Q19 MRT, 3 components, FP32) option 1 measured
@@ -782,7 +791,7 @@ __device__ __forceinline__ void collide_body_smem(const Params& P, typename Prec
 }
 
 template <int Q, int NC, class Prec, int MRT>
-__global__ void __launch_bounds__(kCollideThreads, kCollideBlocks) k_collide(const __grid_constant__ Params P, typename Prec::S* __restrict__ f,
+__global__ void __launch_bounds__(kCollideThreads, kCollideBlocksOf<Q, Prec>) k_collide(const __grid_constant__ Params P, typename Prec::S* __restrict__ f,
                                                        const typename Prec::PsiT* __restrict__ psi,
                                                        const int* status, long long* t_dev, int parity) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -807,7 +816,7 @@ __global__ void __launch_bounds__(kCollideThreads, kCollideBlocks) k_collide(con
 // adjoint's replay keeps every state of a segment; the AA pattern makes the two buffers hold
 // the same slots, so fout needs no copy of fin first).
 template <int Q, int NC, class Prec, int MRT>
-__global__ void __launch_bounds__(kCollideThreads, kCollideBlocks)
+__global__ void __launch_bounds__(kCollideThreads, kCollideBlocksOf<Q, Prec>)
     k_collide_oop(const __grid_constant__ Params P, typename Prec::S* __restrict__ fin, typename Prec::S* __restrict__ fout,
                   const typename Prec::PsiT* __restrict__ psi, const int* status, long long* t_dev, int parity) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
