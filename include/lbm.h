@@ -235,7 +235,11 @@ lbm_status lbm_profile_read(lbm_ctx *ctx, int kernel, double *total_ms, int64_t 
  * (j,i) entries), dgamma[nc] = dL/dgamma_i, drho0[nc][N] = dL/drho at the recorded start for
  * an equilibrium start at rest (lbm_init with u = NULL). Arithmetic in the storage precision
  * (FP32 for LBM_FP32_SHIFTED) with the EOS derivative and the reductions in FP64. Device
- * memory: checkpoint_every states plus four adjoint fields, allocated for the call. */
+ * memory, allocated for the call: checkpoint_every states and pseudo-potential fields plus
+ * the adjoint fields. With full storage (lbm_set_adjoint_memory 0) and more than one segment
+ * it also tries a second set of checkpoint_every states and fields, so that the replay of the
+ * next segment runs on a stream of its own beside the current segment's reverse sweep; where
+ * that set cannot be allocated the two run one after the other (same results bit for bit). */
 lbm_status lbm_record(lbm_ctx *ctx, int64_t n, int checkpoint_every);
 /* Device memory of lbm_adjoint's reverse sweep. snapshots = 0 (the default) or >=
  * checkpoint_every: each recorded segment's states are recomputed once and all kept
@@ -243,7 +247,9 @@ lbm_status lbm_record(lbm_ctx *ctx, int64_t n, int checkpoint_every);
  * checkpointing inside each segment (Griewank's schedule): with s free slots the reversal of n
  * steps advances m of them into a slot, reverses the last n - m with s - 1 slots, then the first
  * m with s, m chosen so that no step is advanced more than r times, r the least integer with
- * C(s + r, s) >= n. snapshots + 2 state slots are allocated; the gradients equal those of the
+ * C(s + 1 + r, s + 1) >= n (s + 1 snapshots, the segment's start included), and the total of
+ * advanced steps the least such a schedule allows. snapshots + 2 state slots are allocated
+ * (two of them scratch for the out-of-place steps); the gradients equal those of the
  * full schedule bit for bit (the recomputed states are identical), at the cost of up to r
  * recomputations per step. */
 lbm_status lbm_set_adjoint_memory(lbm_ctx *ctx, int snapshots);

@@ -94,14 +94,19 @@ struct lbm_ctx {
 
 namespace lbm {
 struct AdjFns {
-  void (*seed)(const Params&, const double*, void*, cudaStream_t);
-  void (*pass_a)(const Params&, const void* f, const void* psi, const void* lam, void* Fb, void* jb, void* rb,
-                 int parity, double* gpart, cudaStream_t);
-  void (*pass_b)(const Params&, const void* f, const void* psi, const void* lam, const void* Fb, const void* jb,
-                 const void* rb, void* lam_out, int parity, double* kpart, cudaStream_t);
-  void (*init_grad)(const Params&, const void* lam, double* drho0, cudaStream_t);
+  void (*seed)(const Params&, const double*, void* X, void* rbB, cudaStream_t);
+  void (*pass_a)(const Params&, const void* f, const void* psi, const void* X, const void* rbB, void* X_out,
+                 void* Fb, void* rho, int parity, double* gpart, cudaStream_t);
+  void (*pass_b)(const Params&, const void* psi, const void* Fb, const void* rho, void* rbB, double* kpart,
+                 cudaStream_t);
+  // pass B of lam(t + 1) (psi_t1, F_in, rho_in) then pass A of step t (f, psi_t, X -> X_out,
+  // F_out, rho_out): one fused launch for D2Q9, the two passes for D3Q19 (through rbB)
+  void (*pass_ab)(const Params&, const void* f, const void* psi_t, const void* psi_t1, const void* X, void* X_out,
+                  const void* F_in, void* F_out, const void* rho_in, void* rho_out, void* rbB, int parity,
+                  double* gpart, double* kpart, cudaStream_t);
+  void (*init_grad)(const Params&, const void* X, const void* rbB, double* drho0, cudaStream_t);
+  unsigned (*rows)(const Params&);  // rows of the partial-sum arrays (one per block of any pass)
   int real_bytes;
-  int block;  // threads per block of the passes (the partial-sum arrays hold one row per block)
 };
 const AdjFns* adj_fns(int Q, int nc, int precision);
 }  // namespace lbm
@@ -165,7 +170,6 @@ double m_factor(double w) {
 int rows_q(int Q, int i) { return Q == 9 ? lbm::Lat<9>::krow(i) : lbm::Lat<19>::krow(i); }
 int nk_q(int Q) { return Q == 9 ? lbm::Lat<9>::NK : lbm::Lat<19>::NK; }
 int norm_q(int Q, int k) { return Q == 9 ? lbm::mnorm<9>(k) : lbm::mnorm<19>(k); }
-double w_q(int Q, int a) { return Q == 9 ? lbm::Lat<9>::w(a) : lbm::Lat<19>::w(a); }
 
 lbm_status ensure_scratch(lbm_ctx* c) {
   if (c->scratch) return LBM_OK;
@@ -1212,12 +1216,16 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
   const int64_t N = c->P.N;
   const int nc = c->nc, Q = c->Q, K = c->ck_every;
   const size_t sbytes = lbm_state_bytes(c), lbytes = (size_t)nc * Q * N * A->real_bytes;
-  const unsigned nblk = (unsigned)((N + A->block - 1) / A->block);  // blocks of pass A / B
+  const unsigned nblk = A->rows(c->P);  // rows of the partial sums: one per block of any pass
   // revolve-style reversal inside each segment with S state slots when S < K; otherwise every
   // state of a segment is recomputed once and kept (K slots)
   const int S = (c->adj_snaps > 0 && c->adj_snaps < K) ? c->adj_snaps : 0;
   std::vector<void*> snaps((size_t)(S > 0 ? S + 2 : K), nullptr);
-  void *la = nullptr, *lb = nullptr, *Fb = nullptr, *jb = nullptr, *rb = nullptr, *psis = nullptr;
+  // lam = X + rbB: X (la / lb, swapped every reverse step) and rbB per site and component.
+  // Fbuf and rhob carry Fbar and the densities from pass A to pass B; pass A writes the pair
+  // the following pass B does not read (index fc ^ 1, fc flipping with every pass A).
+  void *la = nullptr, *lb = nullptr, *rbB = nullptr, *psis = nullptr;
+  void *Fbuf[2] = {nullptr, nullptr}, *rhob[2] = {nullptr, nullptr};
   double *gpart = nullptr, *kpart = nullptr, *dd = nullptr;
   int* st_s = nullptr;
   long long* t_s = nullptr;
@@ -1228,48 +1236,107 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
   for (auto& p : snaps) alloc(&p, sbytes);
   // psi of every state of a segment, computed once by the replay and read by the reverse steps
   const size_t pbytes = (size_t)N * c->ops->psi_bytes;
-  alloc(&psis, (size_t)(S > 0 ? 1 : K) * pbytes);
-  auto psi_of = [&](int i) { return (void*)((char*)psis + (size_t)i * pbytes); };
+  // revolve: plane 0 for the advances, planes 1 and 2 for psi of the last two reversed states
+  alloc(&psis, (size_t)(S > 0 ? 3 : K) * pbytes);
   alloc(&la, lbytes);
   alloc(&lb, lbytes);
-  alloc(&Fb, (size_t)3 * N * A->real_bytes);
-  alloc(&jb, (size_t)3 * N * A->real_bytes);
-  alloc(&rb, (size_t)nc * N * A->real_bytes);
+  for (int i = 0; i < 2; ++i) {
+    alloc(&Fbuf[i], (size_t)3 * N * A->real_bytes);
+    alloc(&rhob[i], (size_t)nc * N * A->real_bytes);
+  }
+  alloc(&rbB, (size_t)nc * N * A->real_bytes);
   alloc((void**)&gpart, (size_t)nblk * nc * sizeof(double));
   alloc((void**)&kpart, (size_t)nblk * nc * nc * sizeof(double));
   alloc((void**)&dd, (size_t)nc * N * sizeof(double));
   alloc((void**)&st_s, sizeof(int));
   alloc((void**)&t_s, sizeof(long long));
+  // Full storage: a second set of segment slots lets the replay of segment k - 1 run on a
+  // stream of its own while segment k is reversed (at small sizes both are latency-bound, and
+  // they share no buffer). Without room for it the two alternate on one stream.
+  std::vector<void*> snaps2;
+  void* psis2 = nullptr;
+  cudaStream_t rs = c->stream;
+  cudaEvent_t ev_rep[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
+  bool two = false;
+  if (e == cudaSuccess && S == 0 && c->ckpt.size() > 1) {
+    bool ok = true;
+    snaps2.assign((size_t)K, nullptr);
+    for (auto& p : snaps2) ok = ok && cudaMalloc(&p, sbytes) == cudaSuccess;
+    ok = ok && cudaMalloc(&psis2, (size_t)K * pbytes) == cudaSuccess;
+    cudaStream_t own = nullptr;
+    ok = ok && cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) == cudaSuccess;
+    if (own) rs = own;
+    for (int i = 0; i < 2; ++i) {
+      ok = ok && cudaEventCreateWithFlags(&ev_rep[i], cudaEventDisableTiming) == cudaSuccess;
+      ok = ok && cudaEventCreateWithFlags(&ev_rev[i], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {  // not an error: the serial order needs none of it
+      cudaGetLastError();
+      for (auto& p : snaps2) cudaFree(p);
+      snaps2.clear();
+      cudaFree(psis2);
+      psis2 = nullptr;
+      if (own) cudaStreamDestroy(own);
+      rs = c->stream;
+      for (int i = 0; i < 2; ++i) {
+        if (ev_rep[i]) cudaEventDestroy(ev_rep[i]);
+        if (ev_rev[i]) cudaEventDestroy(ev_rev[i]);
+        ev_rep[i] = ev_rev[i] = nullptr;
+      }
+    }
+    two = ok;
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(gpart, 0, (size_t)nblk * nc * sizeof(double), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(kpart, 0, (size_t)nblk * nc * nc * sizeof(double), c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(Fb, 0, (size_t)3 * N * A->real_bytes, c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(jb, 0, (size_t)3 * N * A->real_bytes, c->stream);
+  for (int i = 0; i < 2; ++i)
+    if (e == cudaSuccess) e = cudaMemsetAsync(Fbuf[i], 0, (size_t)3 * N * A->real_bytes, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(st_s, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dd, drho, (size_t)nc * N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) {
-    A->seed(c->P, dd, la, c->stream);
+    A->seed(c->P, dd, la, rbB, c->stream);
     e = cudaGetLastError();
   }
-  // The work of one segment after its checkpoint is copied to snaps[0]: recompute states
-  // t_k + 1 .. t_k + len - 1, each step reading snaps[i - 1] and writing snaps[i], keeping psi
-  // of every state; then the reverse steps, which swap la and lb once each.
-  auto segment = [&](int64_t tk, int len, void*& la_, void*& lb_) {
+  // One segment after its checkpoint is copied to slot 0 of a slot set: the replay recomputes
+  // states t_k + 1 .. t_k + len - 1, each step reading slot i - 1 and writing slot i, keeping
+  // psi of every state; the reverse steps then read them and swap la and lb once each.
+  void** set_snaps[2] = {snaps.data(), two ? snaps2.data() : snaps.data()};
+  void* set_psis[2] = {psis, two ? psis2 : psis};
+  auto psi_in = [&](int set, int i) { return (void*)((char*)set_psis[set] + (size_t)i * pbytes); };
+  auto replay = [&](int64_t tk, int len, int set) {
+    void** sn = set_snaps[set];
     cudaError_t r = cudaSuccess;
     for (int i = 1; i < len && r == cudaSuccess; ++i) {
       const int parity = (int)((tk + i - 1) & 1);
-      c->ops->psi(c->P, snaps[i - 1], psi_of(i - 1), st_s, parity, c->stream);
-      c->ops->collide_oop(c->P, snaps[i - 1], snaps[i], psi_of(i - 1), st_s, t_s, parity, c->stream);
+      c->ops->psi(c->P, sn[i - 1], psi_in(set, i - 1), st_s, parity, rs);
+      c->ops->collide_oop(c->P, sn[i - 1], sn[i], psi_in(set, i - 1), st_s, t_s, parity, rs);
       r = cudaGetLastError();
     }
     if (r == cudaSuccess) {
-      c->ops->psi(c->P, snaps[len - 1], psi_of(len - 1), st_s, (int)((tk + len - 1) & 1), c->stream);
+      c->ops->psi(c->P, sn[len - 1], psi_in(set, len - 1), st_s, (int)((tk + len - 1) & 1), rs);
       r = cudaGetLastError();
     }
-    for (int i = len - 1; i >= 0 && r == cudaSuccess; --i) {
-      const int parity = (int)((tk + i) & 1);
-      A->pass_a(c->P, snaps[i], psi_of(i), la_, Fb, jb, rb, parity, gpart, c->stream);
-      A->pass_b(c->P, snaps[i], psi_of(i), la_, Fb, jb, rb, lb_, parity, kpart, c->stream);
+    return r;
+  };
+  // The reverse sweep of a segment: pass A of its last step (lam(t + 1) from the seed or the
+  // previous segment's closing pass B), then pass B + pass A per step down to the first, then
+  // the closing pass B of the first state. fc: la == la0 ? 0 : 1 at the start.
+  auto reverse = [&](int64_t tk, int len, int set, void* la_, void* lb_, int fc) {
+    void** sn = set_snaps[set];
+    int i = len - 1;
+    A->pass_a(c->P, sn[i], psi_in(set, i), la_, rbB, lb_, Fbuf[fc ^ 1], rhob[fc ^ 1], (int)((tk + i) & 1), gpart,
+              c->stream);
+    std::swap(la_, lb_);
+    fc ^= 1;
+    cudaError_t r = cudaGetLastError();
+    for (i = len - 2; i >= 0 && r == cudaSuccess; --i) {
+      A->pass_ab(c->P, sn[i], psi_in(set, i), psi_in(set, i + 1), la_, lb_, Fbuf[fc], Fbuf[fc ^ 1], rhob[fc],
+                 rhob[fc ^ 1], rbB, (int)((tk + i) & 1), gpart, kpart, c->stream);
       std::swap(la_, lb_);
+      fc ^= 1;
+      r = cudaGetLastError();
+    }
+    if (r == cudaSuccess) {
+      A->pass_b(c->P, psi_in(set, 0), Fbuf[fc], rhob[fc], rbB, kpart, c->stream);
       r = cudaGetLastError();
     }
     return r;
@@ -1294,11 +1361,23 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
     }
     return r;
   };
+  void* const la0 = la;  // which X buffer is current: la == la0 after an even number of passes A
+  // One step back, the same launches as the full-storage sweep: psi of its state into the plane
+  // of its parity, pass A alone for a segment's first reversed step, else pass B of the step
+  // after it (whose psi is still in the other plane) with pass A; the segment's closing pass B
+  // follows its revolve.
+  auto psi_rev = [&](int64_t t) { return (void*)((char*)psis + (size_t)(1 + (t & 1)) * pbytes); };
+  bool b_pending = false;
   auto back_step = [&](int64_t t, const void* state) {
     const int parity = (int)(t & 1);
-    c->ops->psi(c->P, state, psis, st_s, parity, c->stream);
-    A->pass_a(c->P, state, psis, la, Fb, jb, rb, parity, gpart, c->stream);
-    A->pass_b(c->P, state, psis, la, Fb, jb, rb, lb, parity, kpart, c->stream);
+    const int fc = la == la0 ? 0 : 1;
+    c->ops->psi(c->P, state, psi_rev(t), st_s, parity, c->stream);
+    if (!b_pending)
+      A->pass_a(c->P, state, psi_rev(t), la, rbB, lb, Fbuf[fc ^ 1], rhob[fc ^ 1], parity, gpart, c->stream);
+    else
+      A->pass_ab(c->P, state, psi_rev(t), psi_rev(t + 1), la, lb, Fbuf[fc], Fbuf[fc ^ 1], rhob[fc], rhob[fc ^ 1], rbB,
+                 parity, gpart, kpart, c->stream);
+    b_pending = true;
     std::swap(la, lb);
     return cudaGetLastError();
   };
@@ -1324,51 +1403,88 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
     if (r == cudaSuccess) r = revolve(t0, m, base, s_);
     return r;
   };
-  // Full segments repeat one launch sequence, which is captured as a graph per (parity of t_k,
-  // which buffer is la) and replayed; a failed capture falls back to direct launches.
-  cudaGraphExec_t gx[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  // Full segments repeat the same launches: the replay is captured as a graph per (parity of
+  // t_k, slot set), the reverse sweep per (parity of t_k, which buffer is la, slot set), and
+  // replayed; a failed capture falls back to direct launches.
   bool capture_ok = true;
-  void* const la0 = la;
+  auto captured = [&](cudaGraphExec_t& g, cudaStream_t st, const std::function<cudaError_t()>& body) {
+    if (!g && capture_ok) {
+      cudaGraph_t graph = nullptr;
+      capture_ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (capture_ok) {
+        const cudaError_t r = body();
+        capture_ok = cudaStreamEndCapture(st, &graph) == cudaSuccess && r == cudaSuccess && graph &&
+                     cudaGraphInstantiate(&g, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+      }
+      if (!capture_ok) {
+        g = nullptr;
+        cudaGetLastError();
+      }
+    }
+    return g ? cudaGraphLaunch(g, st) : body();
+  };
+  cudaGraphExec_t g_rep[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cudaGraphExec_t g_rev[2][2][2] = {{{nullptr, nullptr}, {nullptr, nullptr}}, {{nullptr, nullptr}, {nullptr, nullptr}}};
   const int nseg = (int)c->ckpt.size();
+  auto seg_t = [&](int k) { return c->rec_t0 + (int64_t)k * K; };
+  auto seg_len = [&](int k) { return (int)std::min<int64_t>(K, c->rec_t0 + c->rec_n - seg_t(k)); };
+  auto set_of = [&](int k) { return two ? (k & 1) : 0; };
+  // Replay of segment k on rs, after the reverse sweep that last read its slot set.
+  auto run_replay = [&](int k) {
+    const int set = set_of(k), len = seg_len(k);
+    const int64_t tk = seg_t(k);
+    cudaError_t r = two ? cudaStreamWaitEvent(rs, ev_rev[set], 0) : cudaSuccess;
+    if (r == cudaSuccess) r = cudaMemcpyAsync(set_snaps[set][0], c->ckpt[k], sbytes, cudaMemcpyDeviceToDevice, rs);
+    if (r != cudaSuccess) return r;
+    auto body = [&]() { return replay(tk, len, set); };
+    r = (len == K && K > 1) ? captured(g_rep[tk & 1][set], rs, body) : body();
+    if (r == cudaSuccess && two) r = cudaEventRecord(ev_rep[set], rs);
+    return r;
+  };
+  // Reverse sweep of segment k on the context's stream, after its replay.
+  auto run_reverse = [&](int k) {
+    const int set = set_of(k), len = seg_len(k);
+    const int64_t tk = seg_t(k);
+    cudaError_t r = two ? cudaStreamWaitEvent(c->stream, ev_rep[set], 0) : cudaSuccess;
+    if (r != cudaSuccess) return r;
+    void *a = la, *b = lb;
+    const int fc = la == la0 ? 0 : 1;
+    auto body = [&]() { return reverse(tk, len, set, a, b, fc); };
+    r = (len == K && K > 1) ? captured(g_rev[tk & 1][la == la0 ? 0 : 1][set], c->stream, body) : body();
+    if (len & 1) std::swap(la, lb);
+    if (r == cudaSuccess && two) r = cudaEventRecord(ev_rev[set], c->stream);
+    return r;
+  };
+  if (e == cudaSuccess && S == 0 && nseg > 0) e = run_replay(nseg - 1);
   for (int k = nseg - 1; k >= 0 && e == cudaSuccess; --k) {
-    const int64_t tk = c->rec_t0 + (int64_t)k * K;
-    const int len = (int)std::min<int64_t>(K, c->rec_t0 + c->rec_n - tk);
     if (S > 0) {  // the recorded checkpoint is read, never written
-      e = revolve(tk, len, c->ckpt[k], S);
+      e = revolve(seg_t(k), seg_len(k), c->ckpt[k], S);
+      if (e == cudaSuccess) {
+        const int fc = la == la0 ? 0 : 1;
+        A->pass_b(c->P, psi_rev(seg_t(k)), Fbuf[fc], rhob[fc], rbB, kpart, c->stream);
+        b_pending = false;
+        e = cudaGetLastError();
+      }
       continue;
     }
-    e = cudaMemcpyAsync(snaps[0], c->ckpt[k], sbytes, cudaMemcpyDeviceToDevice, c->stream);
-    if (e != cudaSuccess) break;
-    if (len == K && K > 1) {
-      cudaGraphExec_t& g = gx[tk & 1][la == la0 ? 0 : 1];
-      if (!g && capture_ok) {
-        void *a = la, *b = lb;
-        cudaGraph_t graph = nullptr;
-        capture_ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-        if (capture_ok) {
-          const cudaError_t r = segment(tk, len, a, b);
-          capture_ok = cudaStreamEndCapture(c->stream, &graph) == cudaSuccess && r == cudaSuccess && graph &&
-                       cudaGraphInstantiate(&g, graph, 0) == cudaSuccess;
-          if (graph) cudaGraphDestroy(graph);
-        }
-        if (!capture_ok) {
-          g = nullptr;
-          cudaGetLastError();
-        }
-      }
-      if (g) {
-        e = cudaGraphLaunch(g, c->stream);
-        if (len & 1) std::swap(la, lb);
-        continue;
-      }
-    }
-    e = segment(tk, len, la, lb);
+    if (two && k >= 1) e = run_replay(k - 1);  // runs beside the reverse sweep of segment k
+    if (e == cudaSuccess) e = run_reverse(k);
+    if (e == cudaSuccess && !two && k >= 1) e = run_replay(k - 1);
   }
-  for (auto& row : gx)
+  if (two) {
+    const cudaError_t r = cudaStreamSynchronize(rs);
+    if (e == cudaSuccess) e = r;
+  }
+  for (auto& row : g_rep)
     for (auto& g : row)
       if (g) cudaGraphExecDestroy(g);
+  for (auto& pl : g_rev)
+    for (auto& row : pl)
+      for (auto& g : row)
+        if (g) cudaGraphExecDestroy(g);
   if (e == cudaSuccess && drho0) {
-    A->init_grad(c->P, la, dd, c->stream);
+    A->init_grad(c->P, la, rbB, dd, c->stream);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(drho0, dd, (size_t)nc * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   }
@@ -1379,12 +1495,23 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hst, st_s, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   for (auto& p : snaps) cudaFree(p);
+  for (auto& p : snaps2) cudaFree(p);
   cudaFree(psis);
+  cudaFree(psis2);
+  if (two) {
+    cudaStreamDestroy(rs);
+    for (int i = 0; i < 2; ++i) {
+      cudaEventDestroy(ev_rep[i]);
+      cudaEventDestroy(ev_rev[i]);
+    }
+  }
   cudaFree(la);
   cudaFree(lb);
-  cudaFree(Fb);
-  cudaFree(jb);
-  cudaFree(rb);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(Fbuf[i]);
+    cudaFree(rhob[i]);
+  }
+  cudaFree(rbB);
   cudaFree(gpart);
   cudaFree(kpart);
   cudaFree(dd);
