@@ -1233,7 +1233,12 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
   auto alloc = [&](void** p, size_t b) {
     if (e == cudaSuccess) e = cudaMalloc(p, b);
   };
-  for (auto& p : snaps) alloc(&p, sbytes);
+  // each set of state slots is one allocation, slots 256-byte aligned
+  const size_t sstride = (sbytes + 255) & ~(size_t)255;
+  void* slab = nullptr;
+  alloc(&slab, snaps.size() * sstride);
+  if (e == cudaSuccess)
+    for (size_t i = 0; i < snaps.size(); ++i) snaps[i] = (char*)slab + i * sstride;
   // psi of every state of a segment, computed once by the replay and read by the reverse steps
   const size_t pbytes = (size_t)N * c->ops->psi_bytes;
   // revolve: plane 0 for the advances, planes 1 and 2 for psi of the last two reversed states
@@ -1254,14 +1259,15 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
   // stream of its own while segment k is reversed (at small sizes both are latency-bound, and
   // they share no buffer). Without room for it the two alternate on one stream.
   std::vector<void*> snaps2;
-  void* psis2 = nullptr;
+  void *slab2 = nullptr, *psis2 = nullptr;
   cudaStream_t rs = c->stream;
   cudaEvent_t ev_rep[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
   bool two = false;
   if (e == cudaSuccess && S == 0 && c->ckpt.size() > 1) {
     bool ok = true;
-    snaps2.assign((size_t)K, nullptr);
-    for (auto& p : snaps2) ok = ok && cudaMalloc(&p, sbytes) == cudaSuccess;
+    ok = cudaMalloc(&slab2, (size_t)K * sstride) == cudaSuccess;
+    if (ok)
+      for (int i = 0; i < K; ++i) snaps2.push_back((char*)slab2 + (size_t)i * sstride);
     ok = ok && cudaMalloc(&psis2, (size_t)K * pbytes) == cudaSuccess;
     cudaStream_t own = nullptr;
     ok = ok && cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) == cudaSuccess;
@@ -1272,7 +1278,8 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
     }
     if (!ok) {  // not an error: the serial order needs none of it
       cudaGetLastError();
-      for (auto& p : snaps2) cudaFree(p);
+      cudaFree(slab2);
+      slab2 = nullptr;
       snaps2.clear();
       cudaFree(psis2);
       psis2 = nullptr;
@@ -1494,8 +1501,8 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
   if (e == cudaSuccess) e = cudaMemcpyAsync(hk.data(), kpart, hk.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hst, st_s, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  for (auto& p : snaps) cudaFree(p);
-  for (auto& p : snaps2) cudaFree(p);
+  cudaFree(slab);
+  cudaFree(slab2);
   cudaFree(psis);
   cudaFree(psis2);
   if (two) {
