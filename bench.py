@@ -501,7 +501,7 @@ def adjoint_variant():
     t_back = time.perf_counter() - t0
     out = {"steps": c["steps"], "checkpoint_every": c["checkpoint_every"], "forward_s": t_fwd,
            "recorded_forward_s": t_rec, "backward_s": t_back, "cost_vs_forward": (t_rec + t_back) / t_fwd,
-           "target": 3.0, "loss": float(L), "dL_dk12": zeta.grad.item(), "dL_ds": s.grad.item(),
+           "target": 3.0, "loss": float(L.detach()), "dL_dk12": zeta.grad.item(), "dL_ds": s.grad.item(),
            "timing": "host clock around lbm_step / LatticeRun.apply / loss.backward (each synchronises), "
                      "after one untimed gradient evaluation"}
     if "loss_dk12" in ref:

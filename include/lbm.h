@@ -253,6 +253,11 @@ lbm_status lbm_record(lbm_ctx *ctx, int64_t n, int checkpoint_every);
  * full schedule bit for bit (the recomputed states are identical), at the cost of up to r
  * recomputations per step. */
 lbm_status lbm_set_adjoint_memory(lbm_ctx *ctx, int snapshots);
+/* Test hook: on = 0 makes lbm_adjoint run each segment's replay and reverse sweep one after
+ * the other on the context's stream, as it does when the second set of state slots cannot be
+ * allocated; on = 1 (the default) lets the replay run beside the sweep. The gradients are the
+ * same bit for bit either way. */
+lbm_status lbm_test_adjoint_overlap(lbm_ctx *ctx, int on);
 /* Forward steps the reverse sweep recomputes for one segment of n steps with the given state
  * slots (0 or >= n: n - 1, every state once); host arithmetic only, no device. -1 for n < 1 or
  * snapshots < 0. */

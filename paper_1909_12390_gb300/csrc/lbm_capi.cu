@@ -88,6 +88,7 @@ struct lbm_ctx {
   std::vector<std::pair<std::pair<int64_t, int>, cudaGraphExec_t>> seg_graphs;
   int ck_every = 0;
   int adj_snaps = 0;  // lbm_adjoint: state slots per segment (0: every state of a segment)
+  bool adj_overlap = true;  // lbm_adjoint: replay beside the reverse sweep when memory allows
   int64_t rec_t0 = -1, rec_n = 0;
   std::string err;
 };
@@ -1208,6 +1209,13 @@ lbm_status lbm_set_adjoint_memory(lbm_ctx* c, int snapshots) {
   return LBM_OK;
 }
 
+lbm_status lbm_test_adjoint_overlap(lbm_ctx* c, int on) {
+  if (!c) return LBM_ERR_ARG;
+  if (on != 0 && on != 1) return fail(c, LBM_ERR_ARG, "on must be 0 or 1");
+  c->adj_overlap = on == 1;
+  return LBM_OK;
+}
+
 lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dgamma, double* drho0) {
   if (!c || !drho) return c ? fail(c, LBM_ERR_ARG, "drho is NULL") : LBM_ERR_ARG;
   if (c->rec_t0 < 0 || c->rec_t0 + c->rec_n != c->t)
@@ -1263,7 +1271,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
   cudaStream_t rs = c->stream;
   cudaEvent_t ev_rep[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
   bool two = false;
-  if (e == cudaSuccess && S == 0 && c->ckpt.size() > 1) {
+  if (e == cudaSuccess && S == 0 && c->ckpt.size() > 1 && c->adj_overlap) {
     bool ok = true;
     ok = cudaMalloc(&slab2, (size_t)K * sstride) == cudaSuccess;
     if (ok)

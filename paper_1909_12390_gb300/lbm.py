@@ -28,7 +28,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_init", "lbm_step"
            "lbm_step_static", "lbm_step_static_error", "lbm_batch_create", "lbm_batch_destroy",
            "lbm_batch_init", "lbm_batch_step", "lbm_batch_case_status", "lbm_batch_fields",
            "lbm_batch_get_f", "lbm_batch_tune", "lbm_batch_tune_report", "lbm_batch_sites",
-           "lbm_batch_last_error", "lbm_record", "lbm_adjoint", "lbm_set_adjoint_memory", "lbm_revolve_steps", "lbm_flash", "lbm_flash_error", "lbm_diagnostics")
+           "lbm_batch_last_error", "lbm_record", "lbm_adjoint", "lbm_set_adjoint_memory", "lbm_test_adjoint_overlap", "lbm_revolve_steps", "lbm_flash", "lbm_flash_error", "lbm_diagnostics")
 STATIC_MAX_SITES = 1048576
 PATH_AUTO, PATH_TWO_KERNEL, PATH_FUSED, PATH_TRAILING = 0, 1, 2, 3
 FUSED_TILES, FUSED_PLANES = 1, 3
@@ -149,6 +149,7 @@ def lib() -> ctypes.CDLL:
         L.lbm_record.argtypes = [vp, ctypes.c_int64, ctypes.c_int]
         L.lbm_adjoint.argtypes = [vp, _DP, _DP, _DP, _DP]
         L.lbm_set_adjoint_memory.argtypes = [vp, ctypes.c_int]
+        L.lbm_test_adjoint_overlap.argtypes = [vp, ctypes.c_int]
         L.lbm_revolve_steps.argtypes = [ctypes.c_int64, ctypes.c_int]
         L.lbm_revolve_steps.restype = ctypes.c_int64
         L.lbm_last_error.argtypes = [vp]
@@ -389,6 +390,10 @@ class Lattice:
         """State slots of lbm_adjoint's reverse sweep per segment: 0 keeps every state of a
         segment; fewer than checkpoint_every selects revolve-style binomial checkpointing."""
         self._check(lib().lbm_set_adjoint_memory(self._h, int(snapshots)))
+
+    def test_adjoint_overlap(self, on: bool):
+        """Test hook: False runs each segment's replay and reverse sweep one after the other."""
+        self._check(lib().lbm_test_adjoint_overlap(self._h, int(bool(on))))
 
     def adjoint(self, drho):
         """Back-propagate dL/drho(final) (array (nc, *grid)) through the recorded steps.
