@@ -12,6 +12,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "lbm_core.cuh"
@@ -48,6 +49,12 @@ constexpr int kBlock = 256;
 #endif
 constexpr int kCollideThreads = LBM_COLLIDE_THREADS;
 constexpr int kCollideBlocks = LBM_COLLIDE_BLOCKS;
+// threads per block of the staged collide pass (LBM_COLLIDE_STAGED), which is also the stride
+// of its per-thread copies in shared memory
+#ifndef LBM_COLLIDE_STAGED_THREADS
+#define LBM_COLLIDE_STAGED_THREADS 64
+#endif
+constexpr int kStageThreads = LBM_COLLIDE_STAGED_THREADS;
 template <int Q, class Prec>
 constexpr int kCollideBlocksOf = Q == 19 && sizeof(typename Prec::R) == 8 ? LBM_COLLIDE_BLOCKS_F64 : kCollideBlocks;
 // Per-pair values of a site shared by every component and both passes of the collision
@@ -206,19 +213,28 @@ __device__ __forceinline__ void gong_split(const Params& P, const R (&rc)[NC], R
 // and the total momentum j = sum_c sum_a e_a f_ca. The momentum is summed from the differences
 // of opposite populations: near equilibrium the two are close, so in FP32 each difference is
 // exact and j carries no rounding on the scale of the populations.
-template <int Q, int NC, class Prec, int PAR>
+// SRC = 1: the site's populations were staged by its own thread in shared memory, component
+// C's population a at stg[(C Q + a) kStageThreads] (k_collide_staged); 0: read from their slots.
+template <int Q, int NC, class Prec, int PAR, int SRC = 0>
 __device__ __forceinline__ void site_moments(const Params& P, const typename Prec::S* __restrict__ f, const Site& s,
-                                             typename Prec::R (&dl)[NC], typename Prec::R (&j)[3]) {
+                                             typename Prec::R (&dl)[NC], typename Prec::R (&j)[3],
+                                             const float* stg = nullptr) {
   using R = typename Prec::R;
   using L = Lat<Q>;
   j[0] = j[1] = j[2] = 0;
   For<0, NC>::run([&]<int C>() {
     const typename Prec::S* fc = comp_base<Q>(f, P, C);
-    R acc = (R)fc[AA<Q>::template rd<0, PAR>(P, s)];
+    auto pop = [&]<int A>() -> R {
+      if constexpr (SRC)
+        return (R)stg[(C * Q + A) * kStageThreads];
+      else
+        return (R)fc[AA<Q>::template rd<A, PAR>(P, s)];
+    };
+    R acc = pop.template operator()<0>();
     For<0, L::NPAIR>::run([&]<int K>() {
       constexpr int a = L::pfirst(K), b = L::opp(a);
-      const R va = (R)fc[AA<Q>::template rd<a, PAR>(P, s)];
-      const R vb = (R)fc[AA<Q>::template rd<b, PAR>(P, s)];
+      const R va = pop.template operator()<a>();
+      const R vb = pop.template operator()<b>();
       acc += va + vb;
       const R d = va - vb;
 #pragma unroll
@@ -392,10 +408,11 @@ __device__ __forceinline__ void site_prep(const Params& P, const typename Prec::
 
 // S6 of component C at one site, given the site's shared values: Guo-forced BGK or MRT
 // collision and the in-place AA write (see site_collide_m for the pair arrangement).
-template <int Q, int NC, class Prec, int MRT, int PAR, int C, int GLOBAL = 1, int PT = LBM_COLLIDE_PAIRS>
+template <int Q, int NC, class Prec, int MRT, int PAR, int C, int GLOBAL = 1, int PT = LBM_COLLIDE_PAIRS,
+          int SRC = 0>
 __device__ __forceinline__ void comp_collide(const Params& P, typename Prec::S* __restrict__ f, const Site& s,
                                              const SitePrep<Q, NC, typename Prec::R, PT>& sp,
-                                             typename Prec::S* fo = nullptr) {
+                                             typename Prec::S* fo = nullptr, const float* stg = nullptr) {
   using R = typename Prec::R;
   using L = Lat<Q>;
   constexpr int NP = L::NPAIR;
@@ -480,7 +497,14 @@ __device__ __forceinline__ void comp_collide(const Params& P, typename Prec::S* 
     const R mw = -(R)L::w(a);
     g = fma2(v2(-b3, b3), v2(eu, eu), fma2(v2(mw, mw), v2(t, t), v2(va, vb)));
   };
-  const R v0 = (R)ld_pop(fc + AA<Q>::template rd<0, PAR>(P, so));
+  // population A of this component: from its slot, or (SRC = 1) from the thread's staged copy
+  auto ldp = [&]<int A>() -> R {
+    if constexpr (SRC)
+      return (R)ld_pop(stg + (C * Q + A) * kStageThreads);
+    else
+      return (R)ld_pop(fc + AA<Q>::template rd<A, PAR>(P, so));
+  };
+  const R v0 = ldp.template operator()<0>();
   const R g0 = fmx(-(R)L::w(0), fmx(rc[C], P0, dl[C]), v0);
   R d0 = fmx(gkchi, F0, -om * g0);
   R lm[L::NK];
@@ -494,8 +518,8 @@ __device__ __forceinline__ void comp_collide(const Params& P, typename Prec::S* 
       constexpr int a = L::pfirst(K), b = L::opp(a);
       V2<R> g;
       R Fe, Fo;
-      pair_g(std::integral_constant<int, K>{}, (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, so)),
-             (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, so)), g, Fe, Fo);
+      pair_g(std::integral_constant<int, K>{}, ldp.template operator()<a>(), ldp.template operator()<b>(), g, Fe,
+             Fo);
       // {chi Fe + (g_a + g_b), chi Fo + (g_a - g_b)}
       const V2<R> q = fma2(v2(chi, chi), v2(Fe, Fo), add2(v2(g.x, g.x), v2(g.y, -g.y)));
       cs[pclass<Q>(K)] += q.x;
@@ -543,8 +567,8 @@ __device__ __forceinline__ void comp_collide(const Params& P, typename Prec::S* 
       constexpr int K = GI * G + J;
       if constexpr (K < NP) {
         constexpr int a = L::pfirst(K), b = L::opp(a);
-        va[J] = (R)ld_pop(fc + AA<Q>::template rd<a, PAR>(P, so));
-        vb[J] = (R)ld_pop(fc + AA<Q>::template rd<b, PAR>(P, so));
+        va[J] = ldp.template operator()<a>();
+        vb[J] = ldp.template operator()<b>();
       }
     });
     For<0, G>::run([&]<int J>() {
@@ -603,22 +627,24 @@ __device__ __forceinline__ void comp_collide(const Params& P, typename Prec::S* 
 // In FP32 these keep the rounding of the large quantities out of the momentum balance; a
 // textbook per-direction evaluation lets that rounding drive a random walk of the total
 // momentum, and long runs of a liquid slab then drift measurably.
-template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1, int PT = LBM_COLLIDE_PAIRS>
+template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1, int PT = LBM_COLLIDE_PAIRS, int SRC = 0>
 __device__ __forceinline__ void site_collide_m(const Params& P, typename Prec::S* __restrict__ f, const Site& s,
                                                const typename Prec::R (&pn)[Q], const typename Prec::R (&dl)[NC],
-                                               const typename Prec::R (&j)[3], typename Prec::S* fo = nullptr) {
+                                               const typename Prec::R (&j)[3], typename Prec::S* fo = nullptr,
+                                               const float* stg = nullptr) {
   SitePrep<Q, NC, typename Prec::R, PT> sp;
   site_prep<Q, NC, Prec, PT>(P, pn, dl, j, sp);
-  For<0, NC>::run([&]<int C>() { comp_collide<Q, NC, Prec, MRT, PAR, C, GLOBAL, PT>(P, f, s, sp, fo); });
+  For<0, NC>::run([&]<int C>() { comp_collide<Q, NC, Prec, MRT, PAR, C, GLOBAL, PT, SRC>(P, f, s, sp, fo, stg); });
 }
 
 // S1 and S4-S6 of one site (the moments, then the collision).
-template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1>
+template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1, int SRC = 0>
 __device__ __forceinline__ void site_collide(const Params& P, typename Prec::S* __restrict__ f, const Site& s,
-                                             const typename Prec::R (&pn)[Q], typename Prec::S* fo = nullptr) {
+                                             const typename Prec::R (&pn)[Q], typename Prec::S* fo = nullptr,
+                                             const float* stg = nullptr) {
   typename Prec::R dl[NC], j[3];
-  site_moments<Q, NC, Prec, PAR>(P, f, s, dl, j);
-  site_collide_m<Q, NC, Prec, MRT, PAR, GLOBAL>(P, f, s, pn, dl, j, fo);
+  site_moments<Q, NC, Prec, PAR, SRC>(P, f, s, dl, j, stg);
+  site_collide_m<Q, NC, Prec, MRT, PAR, GLOBAL, LBM_COLLIDE_PAIRS, SRC>(P, f, s, pn, dl, j, fo, stg);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -728,10 +754,10 @@ __global__ void __launch_bounds__(kBlock) k_psi4(const __grid_constant__ Params 
 }
 
 // Pass 2: S4-S6 of every site; psi of the neighbours from global memory.
-template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1>
+template <int Q, int NC, class Prec, int MRT, int PAR, int GLOBAL = 1, int SRC = 0>
 __device__ __forceinline__ void collide_site(const Params& P, typename Prec::S* __restrict__ f,
                                              const typename Prec::PsiT* __restrict__ psi, int x, int y, int z,
-                                             typename Prec::S* fo) {
+                                             typename Prec::S* fo, const float* stg = nullptr) {
   using R = typename Prec::R;
   using L = Lat<Q>;
   Site s;
@@ -740,7 +766,7 @@ __device__ __forceinline__ void collide_site(const Params& P, typename Prec::S* 
   pn[0] = (R)psi[s.idx];
 #pragma unroll
   for (int a = 1; a < Q; ++a) pn[a] = (R)psi[s.nb(P, L::e(a, 0), L::e(a, 1), L::e(a, 2))];
-  site_collide<Q, NC, Prec, MRT, PAR, GLOBAL>(P, f, s, pn, fo);
+  site_collide<Q, NC, Prec, MRT, PAR, GLOBAL, SRC>(P, f, s, pn, fo, stg);
 }
 template <int Q, int NC, class Prec, int MRT, int PAR>
 __device__ __forceinline__ void collide_body(const Params& P, typename Prec::S* __restrict__ f,
@@ -810,6 +836,105 @@ __global__ void __launch_bounds__(kCollideThreads, kCollideBlocksOf<Q, Prec>) k_
     collide_body<Q, NC, Prec, MRT, 1>(P, f, psi, x);
   else
     collide_body<Q, NC, Prec, MRT, 0>(P, f, psi, x);
+}
+
+// LBM_COLLIDE_STAGED = 1 (FP32-shifted storage): the collide pass as a persistent loop over
+// row segments of kStageThreads sites. Each thread copies the populations of its site in the
+// next segment into shared memory (cp.async, 4 bytes each: the copies hold no registers and
+// their latency runs under the current site's collision) and computes the current site from
+// its own staged copy, so the DRAM latency of a site's 57 loads is off its critical path.
+// Each thread reads only what it copied itself: no block barrier. The slots of the next site
+// are disjoint from those the current site writes (every site reads and writes its own set),
+// so the early copy reads values no one writes in this step. Two stages of NC Q kStageThreads
+// floats per block. Measured on GB300 (256^3 sphere workload, bit-identical states): 1.72 ms per
+// collide pass against 1.50 ms for k_collide, so it is off. It removes half of the DRAM-latency
+// stalls but its shared memory (29 KB per 64-thread block, two stages) caps the SM at 12 warps
+// against k_collide's 14.5, and the carve-out leaves L1 too little room for the
+// pseudo-potential stencil.
+#ifndef LBM_COLLIDE_STAGED
+#define LBM_COLLIDE_STAGED 0
+#endif
+#ifndef LBM_COLLIDE_STAGED_BLOCKS
+#define LBM_COLLIDE_STAGED_BLOCKS 6  // 170 registers, no spills; 12 warps per SM
+#endif
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int Q, int NC, class Prec, int MRT, int PAR>
+__device__ __forceinline__ void collide_staged_body(const Params& P, float* __restrict__ f,
+                                                    const float* __restrict__ psi) {
+  extern __shared__ float stage_sm[];
+  constexpr int T = kStageThreads, STAGE = NC * Q * T;
+  const int tid = threadIdx.x;
+  // items (segment, y, z), segment fastest; nseg ny nz <= N < 2^32 / Q fits an int. A block
+  // takes items blockIdx.x, + gridDim.x, ...: the coordinates advance by the mixed-radix digits
+  // of gridDim.x (no division per item)
+  const int nseg = (P.nx + T - 1) / T;
+  const int nitems = nseg * P.ny * P.nz;
+  const int G = (int)gridDim.x, gs = G % nseg, gy = (G / nseg) % P.ny, gz = G / nseg / P.ny;
+  auto advance = [&](int& sg, int& yy, int& zz) {
+    sg += gs;
+    int c = sg >= nseg;
+    sg -= c ? nseg : 0;
+    yy += gy + c;
+    c = yy >= P.ny;
+    yy -= c ? P.ny : 0;
+    zz += gz + c;
+  };
+  // copies of the site (seg, y, z) of this thread, if it has one, into stage buf
+  auto issue = [&](int sg, int yy, int zz, int buf) -> bool {
+    const int x = sg * T + tid;
+    if (x >= P.nx) return false;
+    Site s;
+    s.set_xyz(P, x, yy, zz);
+    float* dst = stage_sm + buf * STAGE + tid;
+    For<0, NC>::run([&]<int C>() {
+      const float* fc = comp_base<Q>((const float*)f, P, C);
+      For<0, Q>::run([&]<int A>() { cp_async4(dst + (C * Q + A) * T, fc + AA<Q>::template rd<A, PAR>(P, s)); });
+    });
+    return true;
+  };
+  int item = (int)blockIdx.x;
+  int seg = item % nseg, y = (item / nseg) % P.ny, z = item / nseg / P.ny;
+  int buf = 0;
+  bool have = item < nitems && issue(seg, y, z, 0);
+  cp_async_commit();
+  while (item < nitems) {
+    const int nxt = item + G;
+    int sn = seg, yn = y, zn = z;
+    advance(sn, yn, zn);
+    const bool have_n = nxt < nitems && issue(sn, yn, zn, buf ^ 1);
+    cp_async_commit();
+    cp_async_wait<1>();  // this thread's copies of the current item have landed
+    if (have)
+      collide_site<Q, NC, Prec, MRT, PAR, 1, 1>(P, f, psi, seg * T + tid, y, z, nullptr, stage_sm + buf * STAGE + tid);
+    item = nxt;
+    seg = sn;
+    y = yn;
+    z = zn;
+    have = have_n;
+    buf ^= 1;
+  }
+  cp_async_wait<0>();
+}
+
+template <int Q, int NC, class Prec, int MRT>
+__global__ void __launch_bounds__(kStageThreads, LBM_COLLIDE_STAGED_BLOCKS)
+    k_collide_staged(const __grid_constant__ Params P, float* __restrict__ f, const float* __restrict__ psi,
+                     const int* status, long long* t_dev, int parity) {
+  if (*(volatile const int*)status) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *t_dev += 1;
+  if (parity)
+    collide_staged_body<Q, NC, Prec, MRT, 1>(P, f, psi);
+  else
+    collide_staged_body<Q, NC, Prec, MRT, 0>(P, f, psi);
 }
 
 // The collide pass out of place: reads the state in fin, writes the next one to fout (the
@@ -1316,6 +1441,23 @@ struct Launch {
   }
   static void collide(const Params& P, void* f, const void* ps, const int* st, long long* t_dev, int parity,
                       cudaStream_t s) {
+    if constexpr (LBM_COLLIDE_STAGED && std::is_same_v<S, float> && std::is_same_v<PsiT, float>) {
+      static int grid = 0;  // resident blocks of the persistent kernel, set once per process
+      constexpr size_t smem = (size_t)2 * NC * Q * kStageThreads * sizeof(float);
+      auto k = k_collide_staged<Q, NC, Prec, MRT>;
+      if (grid == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kStageThreads, smem);
+        grid = sms * (per > 0 ? per : 1);
+      }
+      const long long items = (long long)((P.nx + kStageThreads - 1) / kStageThreads) * P.ny * P.nz;
+      const int g = (int)std::min<long long>(items, grid);
+      k<<<g, kStageThreads, smem, s>>>(P, (float*)f, (const float*)ps, st, t_dev, parity);
+      return;
+    }
     dim3 g, b;
     site_grid(P, g, b, kCollideThreads);
     k_collide<Q, NC, Prec, MRT><<<g, b, 0, s>>>(P, (S*)f, (const PsiT*)ps, st, t_dev, parity);
