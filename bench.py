@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "component-MLUPS (D3Q19 MRT, FP32-shifted populations, FP64 EOS)"
-PATH_NAMES = {1: "two-kernel", 2: "fused", 3: "trailing"}
+PATH_NAMES = {1: "two-kernel", 2: "fused", 3: "trailing", 4: "queue"}
 # what the FP32-shifted path computes in which precision
 EOS_PRECISION = ("FP64: the EOS sums B, A2, the numerator and denominator of p (their cancellation); "
                  "FP32: n_i = rho_i / M_i, the quotient p = pD / Dd, psi = sqrt(psi^2), moments, force, collision; "
@@ -63,6 +63,7 @@ def kernel_source_sha():
     h = hashlib.sha256()
     pkg = os.path.join(ROOT, "paper_1909_12390_gb300")
     files = [os.path.join("csrc", f) for f in ("lbm_core.cuh", "lbm_kernels.cuh", "lbm_fused3.cuh", "lbm_trail3.cuh",
+                                               "lbm_trailq.cuh",
                                                "lbm_ops.h", "lbm_d3q19_f32s_mrt.cu")] + ["build.py"]
     for fn in files:
         with open(os.path.join(pkg, fn), "rb") as fh:
@@ -580,7 +581,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--path", default="auto", choices=["auto", "fused", "two", "trailing"],
+    ap.add_argument("--path", default="auto", choices=["auto", "fused", "two", "trailing", "queue"],
                     help="step path of the timed run (default: the library's choice)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the per-workload error check against the stored oracle runs")
@@ -625,7 +626,8 @@ def main():
 
     gpu = lattice_for(c, lbm.FP64 if args.fp64 else lbm.FP32_SHIFTED)
     if args.path != "auto":
-        gpu.set_path({"fused": lbm.PATH_FUSED, "two": lbm.PATH_TWO_KERNEL, "trailing": lbm.PATH_TRAILING}[args.path])
+        gpu.set_path({"fused": lbm.PATH_FUSED, "two": lbm.PATH_TWO_KERNEL, "trailing": lbm.PATH_TRAILING,
+                      "queue": lbm.PATH_QUEUE}[args.path])
     gpu.init(rho0)
     gpu.step(args.warmup)
     start = torch.cuda.Event(enable_timing=True)
@@ -667,8 +669,8 @@ def main():
     # move exactly that; psi traffic is not counted)
     peak, peak_kind = peaks()
     alg_site = 2 * 19 * nc * (8 if args.fp64 else 4)
-    if path == lbm.PATH_TRAILING:
-        kname, kavg = "k_trail3", fus_ms / max(fus_n, 1)
+    if path in (lbm.PATH_TRAILING, lbm.PATH_QUEUE):
+        kname, kavg = "k_trail3" if path == lbm.PATH_TRAILING else "k_trailq", fus_ms / max(fus_n, 1)
         kinds = {kname: kavg}
         if psi_n:
             kinds["k_psi (first step of the call)"] = psi_ms / psi_n
@@ -726,7 +728,7 @@ def main():
                             "hbm_frac_of_step": (N * 2 * 19 * nc * 8 / (ms64 / 1e3) / 1e9) / peak}
         variants["fp32s"] = {"value": value, "ms_per_step": ms_step, "path": roof["path"]}
         # the same workload on the other step paths
-        for other in (lbm.PATH_TWO_KERNEL, lbm.PATH_TRAILING, lbm.PATH_FUSED):
+        for other in (lbm.PATH_TWO_KERNEL, lbm.PATH_QUEUE, lbm.PATH_TRAILING, lbm.PATH_FUSED):
             if other == path:
                 continue
             g2 = lattice_for(c, lbm.FP32_SHIFTED)

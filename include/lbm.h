@@ -197,9 +197,19 @@ lbm_status lbm_restore(lbm_ctx *ctx, const void *buf, size_t bytes, int64_t t);
  * written to a second psi field. A failing psi (EOS domain, non-finite) ends the step that
  * computed it normally and is reported for the next step, whose index lbm_time then gives,
  * with the populations of the state before it, as on the other paths. */
-enum { LBM_PATH_AUTO = 0, LBM_PATH_TWO_KERNEL = 1, LBM_PATH_FUSED = 2, LBM_PATH_TRAILING = 3 };
+/* LBM_PATH_QUEUE (D3Q19, nz >= 3): one launch per step whose CTAs take the step's tasks from a
+ * ticket counter in a fixed order: the collision of each chunk of 512 consecutive sites of a z
+ * plane (psi of the step computed by the previous step, as on the trailing path), and psi of
+ * the NEXT step for each chunk, placed a plane or two after the collisions it needs and
+ * waiting for them (per-chunk release flags, bounded acquire waits). The populations are read
+ * from DRAM once per step and written once; psi of the next step re-reads them from L2. The
+ * order puts every task a psi task waits for at a smaller ticket, so the queue cannot deadlock
+ * and needs no co-resident launch. Failures are reported as on the trailing path. The same
+ * Section 3.4 step as every other path, bit for bit. */
+enum { LBM_PATH_AUTO = 0, LBM_PATH_TWO_KERNEL = 1, LBM_PATH_FUSED = 2, LBM_PATH_TRAILING = 3, LBM_PATH_QUEUE = 4 };
 lbm_status lbm_set_path(lbm_ctx *ctx, int path);
-/* The path lbm_step takes now (LBM_PATH_TWO_KERNEL, LBM_PATH_FUSED or LBM_PATH_TRAILING). */
+/* The path lbm_step takes now (LBM_PATH_TWO_KERNEL, LBM_PATH_FUSED, LBM_PATH_TRAILING or
+ * LBM_PATH_QUEUE). */
 int lbm_get_path(const lbm_ctx *ctx);
 /* The form of the fused path: LBM_FUSED_TILES or LBM_FUSED_PLANES; 0 on the other paths or
  * for a NULL ctx. */
@@ -208,7 +218,8 @@ int lbm_get_fused_kind(const lbm_ctx *ctx);
 
 /* Failure-detection test hook, fused and trailing paths only: from the next step on, fused
  * block `block` (0-based; LBM_FUSED_TILES: x-tile fastest, then y-tile, then chunk;
- * LBM_FUSED_PLANES and LBM_PATH_TRAILING: the plane range index) computes but never publishes its
+ * LBM_FUSED_PLANES and LBM_PATH_TRAILING: the plane range index; LBM_PATH_QUEUE: the chunk index
+ * of a plane, whose collisions then publish nothing in any plane) computes but never publishes its
  * progress, so every neighbour's bounded wait runs out and lbm_step returns
  * LBM_ERR_TIMEOUT (within about a second per step, without faulting or hanging the GPU); the
  * populations are then undefined. -1 switches the hook off; lbm_init restores a state. */

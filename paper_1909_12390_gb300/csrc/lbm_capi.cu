@@ -301,7 +301,8 @@ void launch_steps(lbm_ctx* c, int64_t n, int64_t t0) {
         e1 = next_event(c);
       }
       if (e0 >= 0) cudaEventRecord(c->ev_pool[e0], c->stream);
-      cudaError_t e = c->fargs.mode == 4 ? c->ops->trail3(c->P, c->f, c->status, c->t_dev, c->fargs, c->stream)
+      cudaError_t e = c->fargs.mode == 5   ? c->ops->trailq(c->P, c->f, c->status, c->t_dev, c->fargs, c->stream)
+                      : c->fargs.mode == 4 ? c->ops->trail3(c->P, c->f, c->status, c->t_dev, c->fargs, c->stream)
                       : c->fargs.mode == 3 ? c->ops->fused3(c->P, c->f, c->status, c->t_dev, c->fargs, c->stream)
                                            : c->ops->fused(c->P, c->f, c->psi, c->status, c->t_dev, c->fargs, c->stream);
       if (e != cudaSuccess && c->launch_err == cudaSuccess) c->launch_err = e;
@@ -342,6 +343,8 @@ void free_fused(lbm_ctx* c) {
   cudaFree((void*)c->fargs.range);
   cudaFree((void*)c->fargs.nbr);
   cudaFree(c->fargs.psi_ring);
+  cudaFree((void*)c->fargs.tasks);
+  cudaFree(c->fargs.ticket);
   c->fargs = lbm::FusedArgs{};
   c->fused = false;
   c->trail_t = -1;
@@ -349,10 +352,12 @@ void free_fused(lbm_ctx* c) {
 
 // Workers (plane ranges) of the plane-range kernel, or blocks of the tile-column kernel.
 int fused_blocks(const lbm_ctx* c) {
+  if (c->fargs.mode == 5) return c->fargs.nch;  // k_trailq: chunks of a plane
   return c->fargs.mode >= 3 ? c->fargs.G : c->fargs.ntx * c->fargs.nty * c->fargs.nchunk;
 }
 // Progress counters of the active fused kernel.
 int fused_flags(const lbm_ctx* c) {
+  if (c->fargs.mode == 5) return c->fargs.nch * c->P.nz;  // one per (plane, chunk)
   return c->fargs.mode == 3 ? c->fargs.G * c->ops->fused3_flags : fused_blocks(c);
 }
 
@@ -493,6 +498,110 @@ bool setup_trail3(lbm_ctx* c) {
        cudaMemset(a.done, 0, sizeof(unsigned int)) == cudaSuccess && cudaMemset(a.pending, 0, sizeof(int)) == cudaSuccess &&
        cudaMemcpy(d_range, range.data(), (G + 1) * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+  c->fargs = a;
+  if (!ok) {
+    cudaGetLastError();
+    free_fused(c);
+    return false;
+  }
+  c->fused = true;
+  c->trail_t = -1;
+  return true;
+}
+
+// The task-queue one-pass step (k_trailq, D3Q19): each plane cut into nch chunks of
+// ops->trailq_chunk consecutive sites of the flattened (y, x) index; per chunk the chunks
+// holding the in-plane neighbours of its sites; the ticket order of the step's tasks (every
+// collision in plane order, the psi task of (z, c) after the collision of (z + 1 + lag, c), the
+// psi tasks of planes nz - 1 and 0 last), checked here to place every task a psi task waits for
+// at a smaller ticket; one progress flag per (plane, chunk); two psi fields. As many CTAs as
+// the device holds at once (fewer would also be correct: see the kernel's header).
+bool setup_trailq(lbm_ctx* c) {
+  free_fused(c);
+  if (c->Q != 19 || !c->ops->trailq_max_blocks) return false;
+  const int nx = c->P.nx, ny = c->P.ny, nz = c->P.nz;
+  const long long nxy = (long long)nx * ny;
+  if (nz < 3 || nxy < 1) return false;
+  const int cap = c->ops->trailq_max_blocks();
+  if (cap <= 0) return false;
+  const int TS = (int)std::min<long long>(c->ops->trailq_chunk, nxy);
+  const int nch = (int)((nxy + TS - 1) / TS);
+  if ((long long)nch * nz * 2 >= (1LL << 30)) return false;
+  const int K = lbm::kF3MaxNbr;
+  std::vector<int> nbr((size_t)nch * K, -1);
+  for (int ch = 0; ch < nch; ++ch) {
+    int n = 0;
+    const long long hi = std::min<long long>((long long)(ch + 1) * TS, nxy);
+    for (long long i = (long long)ch * TS; i < hi; ++i) {
+      const int x = (int)(i % nx), y = (int)(i / nx);
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int o = (int)((((long long)((y + dy + ny) % ny)) * nx + (x + dx + nx) % nx) / TS);
+          if (o == ch) continue;
+          bool seen = false;
+          for (int k = 0; k < n; ++k) seen = seen || nbr[(size_t)ch * K + k] == o;
+          if (seen) continue;
+          if (n == K) return false;
+          nbr[(size_t)ch * K + n++] = o;
+        }
+    }
+  }
+  // ticket order
+  const int lag = c->ops->trailq_lag;
+  const long long ncol = (long long)nz * nch;
+  std::vector<int> tasks;
+  tasks.reserve((size_t)(2 * ncol));
+  std::vector<char> placed((size_t)ncol, 0);
+  for (long long i = 0; i < ncol; ++i) {
+    tasks.push_back((int)i);
+    const long long zp = i / nch - 1 - lag, cp = i % nch;
+    if (zp >= 1 && zp <= nz - 2) {
+      tasks.push_back((int)(-(zp * nch + cp) - 1));
+      placed[(size_t)(zp * nch + cp)] = 1;
+    }
+  }
+  for (int z = 1; z < nz; ++z)
+    for (int ch = 0; ch < nch; ++ch)
+      if (!placed[(size_t)z * nch + ch]) tasks.push_back(-(z * nch + ch) - 1);
+  for (int ch = 0; ch < nch; ++ch) tasks.push_back(-ch - 1);
+  // every collision a psi task needs has a smaller ticket
+  std::vector<long long> pos((size_t)ncol, -1);
+  for (size_t p = 0; p < tasks.size(); ++p)
+    if (tasks[p] >= 0) pos[(size_t)tasks[p]] = (long long)p;
+  for (size_t p = 0; p < tasks.size(); ++p) {
+    if (tasks[p] >= 0) continue;
+    const int q = -tasks[p] - 1, z = q / nch, ch = q % nch;
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int zz = (z + dz + nz) % nz;
+      for (int j = -1; j < K && (j < 0 || nbr[(size_t)ch * K + j] >= 0); ++j) {
+        const int cc = j < 0 ? ch : nbr[(size_t)ch * K + j];
+        const long long pc = pos[(size_t)zz * nch + cc];
+        if (pc < 0 || pc >= (long long)p) return false;
+      }
+    }
+  }
+  lbm::FusedArgs a{};
+  a.mode = 5;
+  a.G = (int)std::min<long long>(cap, (long long)tasks.size());
+  a.smax = TS;
+  a.nch = nch;
+  a.ntask = (int)tasks.size();
+  a.silent_block = -1;
+  int* d_nbr = nullptr;
+  int* d_tasks = nullptr;
+  bool ok = cudaMalloc(&a.flags, (size_t)ncol * sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMalloc(&a.done, sizeof(unsigned int)) == cudaSuccess && cudaMalloc(&a.pending, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&a.ticket, sizeof(unsigned int)) == cudaSuccess &&
+            cudaMalloc(&d_nbr, nbr.size() * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&d_tasks, tasks.size() * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&a.psi_ring, (size_t)2 * c->P.N * c->ops->psi_bytes) == cudaSuccess;
+  a.nbr = d_nbr;
+  a.tasks = d_tasks;
+  ok = ok && cudaMemset(a.flags, 0, (size_t)ncol * sizeof(unsigned long long)) == cudaSuccess &&
+       cudaMemset(a.done, 0, sizeof(unsigned int)) == cudaSuccess && cudaMemset(a.pending, 0, sizeof(int)) == cudaSuccess &&
+       cudaMemset(a.ticket, 0, sizeof(unsigned int)) == cudaSuccess &&
+       cudaMemcpy(d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(d_tasks, tasks.data(), tasks.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
   c->fargs = a;
   if (!ok) {
     cudaGetLastError();
@@ -872,7 +981,7 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n) {
   if (!c) return LBM_ERR_ARG;
   if (n < 0) return fail(c, LBM_ERR_ARG, "n must be >= 0");
   int64_t t = c->t, left = n;
-  const bool trailing = c->fused && c->fargs.mode == 4;
+  const bool trailing = c->fused && c->fargs.mode >= 4;
   if (trailing && n > 0 && c->trail_t != t) {
     // psi of the first step, which the trailing step reads from psi_ring[t & 1]
     const int e0 = c->profiling ? next_event(c) : -1, e1 = c->profiling ? next_event(c) : -1;
@@ -911,7 +1020,8 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n) {
 
 lbm_status lbm_set_path(lbm_ctx* c, int path) {
   if (!c) return LBM_ERR_ARG;
-  if (path != LBM_PATH_AUTO && path != LBM_PATH_TWO_KERNEL && path != LBM_PATH_FUSED && path != LBM_PATH_TRAILING)
+  if (path != LBM_PATH_AUTO && path != LBM_PATH_TWO_KERNEL && path != LBM_PATH_FUSED && path != LBM_PATH_TRAILING &&
+      path != LBM_PATH_QUEUE)
     return fail(c, LBM_ERR_ARG, "unknown path %d", path);
   CK(c, cudaStreamSynchronize(c->stream));
   drop_graph(c);
@@ -928,6 +1038,11 @@ lbm_status lbm_set_path(lbm_ctx* c, int path) {
   if (path == LBM_PATH_TRAILING) {
     if (!setup_trail3(c))
       return fail(c, LBM_ERR_ARG, "the trailing step needs D3Q19, nz >= 3 and co-resident CTAs for this grid");
+    return LBM_OK;
+  }
+  if (path == LBM_PATH_QUEUE) {
+    if (!setup_trailq(c))
+      return fail(c, LBM_ERR_ARG, "the task-queue step needs D3Q19 and nz >= 3");
     return LBM_OK;
   }
   if (!setup_fused(c))
@@ -950,11 +1065,12 @@ lbm_status lbm_test_silence_block(lbm_ctx* c, int block) {
 int lbm_get_path(const lbm_ctx* c) {
   if (!c) return -1;
   if (!c->fused) return LBM_PATH_TWO_KERNEL;
+  if (c->fargs.mode == 5) return LBM_PATH_QUEUE;
   return c->fargs.mode == 4 ? LBM_PATH_TRAILING : LBM_PATH_FUSED;
 }
 
 int lbm_get_fused_kind(const lbm_ctx* c) {
-  if (!c || !c->fused || c->fargs.mode == 4) return 0;
+  if (!c || !c->fused || c->fargs.mode >= 4) return 0;
   return c->fargs.mode == 3 ? LBM_FUSED_PLANES : LBM_FUSED_TILES;
 }
 
@@ -1112,7 +1228,7 @@ lbm_status lbm_record(lbm_ctx* c, int64_t n, int checkpoint_every) {
   // count and parity of its first step) after a copy of its starting state; the stream is
   // synchronised once at the end. The trailing step keeps psi between steps and is driven
   // through lbm_step instead.
-  const bool trailing = c->fused && c->fargs.mode == 4;
+  const bool trailing = c->fused && c->fargs.mode >= 4;
   for (int64_t done = 0, i = 0; done < n; ++i) {
     void* p = (char*)c->ckpt_base + (size_t)i * bytes;
     c->ckpt.push_back(p);

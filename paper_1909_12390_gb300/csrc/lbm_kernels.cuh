@@ -131,18 +131,26 @@ __device__ __forceinline__ int site_psi_dl(const Params& P, const typename Prec:
 }
 
 // Shifted densities of one site, summed in the same order as site_moments (rest, then the
-// pairs), so that every path computes bit-identical densities.
-template <int Q, int NC, class Prec, int PAR>
+// pairs), so that every path computes bit-identical densities. CG = 1 loads through L2 only
+// (ld.global.cg): for populations that other SMs wrote earlier in the same launch, which a
+// line left in this SM's L1 by an earlier read could otherwise shadow.
+template <int Q, int NC, class Prec, int PAR, int CG = 0>
 __device__ __forceinline__ void site_densities(const Params& P, const typename Prec::S* __restrict__ f,
                                                const Site& s, typename Prec::R (&d)[NC]) {
   using R = typename Prec::R;
   using L = Lat<Q>;
   For<0, NC>::run([&]<int C>() {
     const typename Prec::S* fc = comp_base<Q>(f, P, C);
-    R acc = (R)fc[AA<Q>::template rd<0, PAR>(P, s)];
+    auto ld = [&](uint32_t o) -> R {
+      if constexpr (CG)
+        return (R)__ldcg(fc + o);
+      else
+        return (R)fc[o];
+    };
+    R acc = ld(AA<Q>::template rd<0, PAR>(P, s));
     For<0, L::NPAIR>::run([&]<int K>() {
       constexpr int a = L::pfirst(K), b = L::opp(a);
-      acc += (R)fc[AA<Q>::template rd<a, PAR>(P, s)] + (R)fc[AA<Q>::template rd<b, PAR>(P, s)];
+      acc += ld(AA<Q>::template rd<a, PAR>(P, s)) + ld(AA<Q>::template rd<b, PAR>(P, s));
     });
     d[C] = acc;
   });
@@ -150,11 +158,11 @@ __device__ __forceinline__ void site_densities(const Params& P, const typename P
 
 // S1-S3 of one site: cell-volume densities, mixture Peng-Robinson EOS, pseudo-potential.
 // Returns 0 or status bits; psi_out is 0 on error.
-template <int Q, int NC, class Prec, int PAR>
+template <int Q, int NC, class Prec, int PAR, int CG = 0>
 __device__ __forceinline__ int site_psi(const Params& P, const typename Prec::S* __restrict__ f, const Site& s,
                                         typename Prec::PsiT& psi_out) {
   typename Prec::R d[NC];
-  site_densities<Q, NC, Prec, PAR>(P, f, s, d);
+  site_densities<Q, NC, Prec, PAR, CG>(P, f, s, d);
   return site_psi_dl<NC, Prec>(P, d, psi_out);
 }
 
@@ -988,11 +996,19 @@ struct FusedArgs {
   int silent_block;           // test hook: this block publishes no progress (-1: none)
   // plane-range form (k_fused3, D3Q19)
   int mode;                   // 1 (or 0): tile columns (k_fused), 3: plane ranges (k_fused3),
-                              // 4: plane ranges with trailing psi (k_trail3)
+                              // 4: plane ranges with trailing psi (k_trail3),
+                              // 5: task queue with trailing psi (k_trailq)
   const int* range;           // G + 1 range starts in the flattened (y, x) index of a plane
   const int* nbr;             // G x kF3MaxNbr workers owning neighbour sites, -1 padded
-  void* psi_ring;             // k_fused3: (kF3Ring + 2) psi planes; k_trail3: two psi fields
-  int G, smax;                // workers (two per CTA), largest range
+                              // (k_trailq: nch x kF3MaxNbr chunks)
+  void* psi_ring;             // k_fused3: (kF3Ring + 2) psi planes; k_trail3, k_trailq: two psi fields
+  int G, smax;                // workers (two per CTA), largest range; k_trailq: CTAs, sites per chunk
+  // task-queue form (k_trailq, mode 5): the ticket order of the step's tasks (collision of
+  // chunk c of plane z: z nch + c; psi of the next step there: -(z nch + c) - 1), the ticket
+  // counter, chunks per plane
+  const int* tasks;
+  int ntask, nch;
+  unsigned int* ticket;
 };
 
 constexpr unsigned kSpinLimit = 1u << 20;  // polls of one flag before giving up (~1 s)
@@ -1407,6 +1423,7 @@ __global__ void k_mass_final(const double* partial, int nblocks, int nc, MassShi
 
 #include "lbm_fused3.cuh"
 #include "lbm_trail3.cuh"
+#include "lbm_trailq.cuh"
 
 namespace lbm {
 
@@ -1544,6 +1561,28 @@ struct Launch {
                                          dim3(kT3Threads), args, 0, s);
     }
   }
+  static int trailq_max_blocks() {
+    if constexpr (Q != 19) {
+      return 0;
+    } else {
+      int nb = 0, dev = 0, sms = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trailq<NC, Prec, MRT>, kTQThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+      }
+      return nb * sms;
+    }
+  }
+  static cudaError_t trailq(const Params& P, void* f, int* st, long long* t_dev, const FusedArgs& A, cudaStream_t s) {
+    if constexpr (Q != 19) {
+      return cudaErrorNotSupported;
+    } else {
+      k_trailq<NC, Prec, MRT><<<(unsigned)A.G, kTQThreads, 0, s>>>(P, (S*)f, st, t_dev, A);
+      return cudaGetLastError();
+    }
+  }
   static void init(const Params& P, void* f, const double* rho, const double* u, cudaStream_t s) {
     k_init<Q, NC, Prec><<<blocks(P), kBlock, 0, s>>>(P, (S*)f, rho, u);
   }
@@ -1570,7 +1609,8 @@ struct Launch {
                             fused3_max_blocks, init,          get_f,        set_f,            fields,
                             mass,          (int)sizeof(S),    (int)sizeof(PsiT), (int)sizeof(R), Fused<Q>::TX,
                             Fused<Q>::TY,  Fused<Q>::P,       kF3WorkersPerCta,  kF3FlagSets,       collide_oop,
-                            trail3,        trail3_max_blocks};
+                            trail3,        trail3_max_blocks, trailq,     trailq_max_blocks, kTQChunk,
+                            kTQLag};
     return &ops;
   }
 };

@@ -40,6 +40,12 @@ struct Ops {
   // from A.psi_ring[t & 1], psi of the next step into A.psi_ring[(t + 1) & 1]
   cudaError_t (*trail3)(const Params&, void* f, int* status, long long* t_dev, const FusedArgs&, cudaStream_t);
   int (*trail3_max_blocks)();  // co-resident CTAs of the trailing step on this device
+  // task-queue one-pass step (D3Q19 only; cudaErrorNotSupported / 0 otherwise), psi fields as
+  // for trail3
+  cudaError_t (*trailq)(const Params&, void* f, int* status, long long* t_dev, const FusedArgs&, cudaStream_t);
+  int (*trailq_max_blocks)();  // resident CTAs of the task-queue step on this device
+  int trailq_chunk;            // sites per task
+  int trailq_lag;              // planes between a collision and the psi task placed after it
 };
 
 // one translation unit per lattice, storage type and collision

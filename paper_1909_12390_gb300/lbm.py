@@ -30,7 +30,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_init", "lbm_step"
            "lbm_batch_get_f", "lbm_batch_tune", "lbm_batch_tune_report", "lbm_batch_sites",
            "lbm_batch_last_error", "lbm_record", "lbm_adjoint", "lbm_set_adjoint_memory", "lbm_test_adjoint_overlap", "lbm_revolve_steps", "lbm_flash", "lbm_flash_error", "lbm_diagnostics")
 STATIC_MAX_SITES = 1048576
-PATH_AUTO, PATH_TWO_KERNEL, PATH_FUSED, PATH_TRAILING = 0, 1, 2, 3
+PATH_AUTO, PATH_TWO_KERNEL, PATH_FUSED, PATH_TRAILING, PATH_QUEUE = 0, 1, 2, 3, 4
 FUSED_TILES, FUSED_PLANES = 1, 3
 SPLIT_VOLATILITY, SPLIT_GONG = 0, 1
 

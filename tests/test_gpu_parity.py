@@ -457,8 +457,8 @@ def test_sphere_mrt_fp32_at_its_stated_step_count(cases):
     oracle run (tests/golden/make_long_runs.py): the same mixture, temperature, pressure, MRT
     rates and liquid fraction on a 96^3 box with R = 18 (the oracle cannot step 256^3 5000
     times on the host). Densities at 4194 sampled sites (a line through the centre, the centre,
-    a corner and SplitMix64 draws) within 2e-4 of the oracle, on the two-kernel and the
-    trailing path (which agree bit for bit); per-component mass against the oracle's."""
+    a corner and SplitMix64 draws) within 2e-4 of the oracle, on the two-kernel, trailing and
+    queue paths (which agree bit for bit); per-component mass against the oracle's."""
     from paper_1909_12390_gb300 import lbm
     p = os.path.join(GOLDEN, "long_runs.npz")
     ref = dict(np.load(p)) if os.path.exists(p) else {}
@@ -469,7 +469,7 @@ def test_sphere_mrt_fp32_at_its_stated_step_count(cases):
     rho0 = initial_rho(dict(c, init=dict(c["init"], radius=float(ref["sphere_radius"]))), shape)
     zs, ys, xs = ref["sphere_sites"]
     states = []
-    for path in (lbm.PATH_TWO_KERNEL, lbm.PATH_TRAILING):
+    for path in (lbm.PATH_TWO_KERNEL, lbm.PATH_TRAILING, lbm.PATH_QUEUE):
         gpu = gpu_lattice(c, shape, FP32S)
         gpu.set_path(path)
         gpu.init(rho0)
@@ -485,3 +485,4 @@ def test_sphere_mrt_fp32_at_its_stated_step_count(cases):
         assert merr < 1e-5
         gpu.close()
     assert np.array_equal(states[0], states[1])
+    assert np.array_equal(states[0], states[2])

@@ -1,7 +1,8 @@
-"""The trailing fused step (LBM_PATH_TRAILING: one persistent launch per step, psi of the next
-step computed from the just-written populations a few planes behind the collision) against
-the two-kernel step, bit for bit, and against the FP64 oracle; its failure semantics and its
-bounded waits."""
+"""The one-pass steps whose psi of the next step trails the collisions (LBM_PATH_TRAILING: one
+persistent launch per step, psi of the next step computed from the just-written populations a
+few planes behind the collision; LBM_PATH_QUEUE: the same two kinds of work as tasks taken from
+a ticket counter) against the two-kernel step, bit for bit, and against the FP64 oracle; their
+failure semantics and their bounded waits."""
 import json
 import os
 
@@ -24,13 +25,19 @@ def cases():
         return json.load(fh)
 
 
-def _pair(c, shape, precision, collision, rates, **kw):
+@pytest.fixture(params=["trailing", "queue"])
+def trail_path(request):
+    from paper_1909_12390_gb300 import lbm
+    return {"trailing": lbm.PATH_TRAILING, "queue": lbm.PATH_QUEUE}[request.param]
+
+
+def _pair(c, shape, precision, collision, rates, path, **kw):
     from paper_1909_12390_gb300 import lbm
     a = gpu_lattice(c, shape, precision, collision=collision, s=rates, **kw)
     b = gpu_lattice(c, shape, precision, collision=collision, s=rates, **kw)
-    a.set_path(lbm.PATH_TRAILING)
+    a.set_path(path)
     b.set_path(lbm.PATH_TWO_KERNEL)
-    assert a.path == lbm.PATH_TRAILING and b.path == lbm.PATH_TWO_KERNEL
+    assert a.path == path and b.path == lbm.PATH_TWO_KERNEL
     return a, b
 
 
@@ -46,12 +53,12 @@ def _ball(c, shape):
                                    (24, 24, 3)])
 @pytest.mark.parametrize("precision", [FP64, FP32S])
 @pytest.mark.parametrize("collision", [0, 1])
-def test_trailing_equals_two_kernel_bitwise(cases, shape, precision, collision):
+def test_trailing_equals_two_kernel_bitwise(cases, shape, precision, collision, trail_path):
     """The collision is the same per-site code and psi of the next step is computed from the
     same slots in the same order, so every population agrees bit for bit after any number of
     steps, over several lbm_step calls (psi carried over between calls) and both parities."""
     c = cases["c3"]
-    a, b = _pair(c, shape, precision, collision, c["mrt_s"])
+    a, b = _pair(c, shape, precision, collision, c["mrt_s"], trail_path)
     rho = _ball(c, shape)
     a.init(rho)
     b.init(rho)
@@ -65,11 +72,11 @@ def test_trailing_equals_two_kernel_bitwise(cases, shape, precision, collision):
 
 
 @pytest.mark.parametrize("nc", [1, 2, 4])
-def test_trailing_equals_two_kernel_other_component_counts(cases, nc):
+def test_trailing_equals_two_kernel_other_component_counts(cases, nc, trail_path):
     from test_gpu_parity import _mixture
     c = _mixture(cases, nc)
     shape = (48, 20, 12)
-    a, b = _pair(c, shape, FP32S, 1, cases["c3"]["mrt_s"])
+    a, b = _pair(c, shape, FP32S, 1, cases["c3"]["mrt_s"], trail_path)
     rho = random_rho(c, tuple(reversed(shape)), seed=3 + nc)
     a.init(rho)
     b.init(rho)
@@ -78,14 +85,14 @@ def test_trailing_equals_two_kernel_other_component_counts(cases, nc):
     assert np.array_equal(a.save()[0], b.save()[0])
 
 
-def test_trailing_long_run_with_graph_replay_and_state_changes(cases):
+def test_trailing_long_run_with_graph_replay_and_state_changes(cases, trail_path):
     """130 steps (two captured 64-step graphs and direct launches), then a restore of an earlier
     state and a re-initialisation: psi is recomputed whenever the state changed outside the
     trailing step."""
     from paper_1909_12390_gb300 import lbm
     c = cases["c3"]
     shape = (64, 40, 20)
-    a, b = _pair(c, shape, FP32S, 1, c["mrt_s"])
+    a, b = _pair(c, shape, FP32S, 1, c["mrt_s"], trail_path)
     rho = _ball(c, shape)
     a.init(rho)
     b.init(rho)
@@ -102,7 +109,7 @@ def test_trailing_long_run_with_graph_replay_and_state_changes(cases):
     assert np.array_equal(a.save()[0], b.save()[0])
     a.set_path(lbm.PATH_TWO_KERNEL)
     a.step(1)
-    a.set_path(lbm.PATH_TRAILING)
+    a.set_path(trail_path)
     b.step(1)
     a.step(2)
     b.step(2)
@@ -114,7 +121,7 @@ def test_trailing_long_run_with_graph_replay_and_state_changes(cases):
     assert np.array_equal(a.save()[0], b.save()[0])
 
 
-def test_trailing_matches_oracle(cases):
+def test_trailing_matches_oracle(cases, trail_path):
     c = cases["c3"]
     shape = (20, 18, 16)
     rates = c["mrt_s"]
@@ -122,7 +129,7 @@ def test_trailing_matches_oracle(cases):
     for precision, tol in ((FP64, 1e-12), (FP32S, 2e-4)):
         ocase = oracle_case(c, shape, collision=1, s=rates)
         gpu = gpu_lattice(c, shape, precision, collision=1, s=rates)
-        gpu.set_path(lbm.PATH_TRAILING)
+        gpu.set_path(trail_path)
         rho = random_rho(c, ocase.grid, seed=9)
         gpu.init(rho)
         f = oracle.equilibrium(ocase, rho)
@@ -134,7 +141,7 @@ def test_trailing_matches_oracle(cases):
         gpu.close()
 
 
-def test_trailing_failure_reports_the_same_step_as_the_two_kernel_path(cases):
+def test_trailing_failure_reports_the_same_step_as_the_two_kernel_path(cases, trail_path):
     """A momentum kick planted at one site (the density there unchanged) makes the step after
     it leave the EOS's domain. The trailing step finds that in its psi stage for the next step;
     both paths report the same status at the same step index, with the same populations (the
@@ -142,7 +149,7 @@ def test_trailing_failure_reports_the_same_step_as_the_two_kernel_path(cases):
     from paper_1909_12390_gb300 import lbm
     c = cases["c3"]
     shape = (32, 24, 12)
-    a, b = _pair(c, shape, FP64, 0, None)
+    a, b = _pair(c, shape, FP64, 0, None, trail_path)
     rho = _ball(c, shape)
     a.init(rho)
     b.init(rho)
@@ -173,17 +180,18 @@ def test_trailing_failure_reports_the_same_step_as_the_two_kernel_path(cases):
     assert np.array_equal(a.save()[0], b.save()[0])
 
 
-def test_trailing_silent_cta_times_out_and_context_recovers(cases):
-    """A CTA that never publishes its progress makes its neighbours' bounded waits run out: the
-    step returns LBM_ERR_TIMEOUT within seconds, the GPU stays usable, and after lbm_init the
-    context steps normally again."""
+def test_trailing_silent_cta_times_out_and_context_recovers(cases, trail_path):
+    """A CTA (trailing path) or a chunk's collision tasks (queue path) that never publish their
+    progress make the bounded waits of the psi work that needs them run out: the step returns
+    LBM_ERR_TIMEOUT within seconds, the GPU stays usable, and after lbm_init the context steps
+    normally again."""
     import time
     from paper_1909_12390_gb300 import lbm
     c = cases["c3"]
     shape = (64, 16, 16)
     rho = initial_rho(dict(c, init=dict(kind="ball", radius=5.0, width=4.0)), shape)
     gpu = gpu_lattice(c, shape, FP32S)
-    gpu.set_path(lbm.PATH_TRAILING)
+    gpu.set_path(trail_path)
     gpu.init(rho)
     gpu.step(2)
     gpu.test_silence_block(1)
@@ -203,12 +211,12 @@ def test_trailing_silent_cta_times_out_and_context_recovers(cases):
 
 
 @pytest.mark.parametrize("shape", [(30, 8, 2), (30, 8)])
-def test_trailing_rejected_when_the_grid_does_not_fit(cases, shape):
+def test_trailing_rejected_when_the_grid_does_not_fit(cases, shape, trail_path):
     from paper_1909_12390_gb300 import lbm
     c = cases["c3"] if len(shape) == 3 else cases["c2"]
     gpu = gpu_lattice(c, shape, FP32S)
     with pytest.raises(lbm.LBMError) as ei:
-        gpu.set_path(lbm.PATH_TRAILING)
+        gpu.set_path(trail_path)
     assert ei.value.status == lbm.ERR_ARG
     assert gpu.path == lbm.PATH_TWO_KERNEL
     gpu.close()
