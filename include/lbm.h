@@ -234,13 +234,13 @@ lbm_status lbm_test_silence_block(lbm_ctx *ctx, int block);
 lbm_status lbm_profile(lbm_ctx *ctx, int on);
 lbm_status lbm_profile_read(lbm_ctx *ctx, int kernel, double *total_ms, int64_t *launches);
 
-/* ---- Adjoint (gradients; BGK collision) ----------------------------------------------
+/* ---- Adjoint (gradients; BGK or MRT collision) ---------------------------------------
  * lbm_record advances n steps from the current state like lbm_step and keeps a copy of the
  * raw state every checkpoint_every steps (the first at the current step). lbm_adjoint then
  * back-propagates dL/drho of the final state (host array drho[nc][N], the loss gradient with
  * respect to the cell-volume densities the recorded run ended with) through every recorded step
- * with the hand-written discrete adjoint of the step (collision with Guo forcing, split of
- * Eq. distributionforce, force of Eq. coupledMCforce, EOS of Eq. MCPengRobinson),
+ * with the hand-written discrete adjoint of the step (BGK or MRT collision with Guo forcing,
+ * split of Eq. distributionforce, force of Eq. coupledMCforce, EOS of Eq. MCPengRobinson),
  * recomputing each segment's states from its checkpoint. Outputs (any may be NULL):
  * dkij[nc*nc] = dL/dzeta_ij per matrix entry (for a symmetric coefficient add the (i,j) and
  * (j,i) entries), dgamma[nc] = dL/dgamma_i, drho0[nc][N] = dL/drho at the recorded start for

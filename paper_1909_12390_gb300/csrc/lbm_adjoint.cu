@@ -22,6 +22,10 @@
 // what it has at hand, and rbB_s, written by pass B, which is added wherever lam is read (the
 // next pass A's gather, the final dL/drho(0)). So pass B reads neither the populations nor
 // lam: only psi, Fbar and the densities pass A leaves behind.
+// MRT (f* = f - K (f - feq) + (I - K/2) chi_s Fb with K = w I + M^T Lam M over the rows whose
+// rate differs from w, M the orthogonal moment basis, so K is symmetric): the same formulas with
+// the moments of mu = K lam* where BGK has w times those of lam*, and the moments of
+// nu = lam* - mu / 2 where it has gk times them; X_sa = lam*_sa - mu_sa + rbar_s + (ubar/rho).e_a.
 // Parameter gradients: dL/dgamma_k = sum_x rho_k (chibar_k - sum chibar chi) / Gam and
 // dL/dzeta_ij = sum_x pbar n_i n_j sqrt(a_i alpha_i a_j alpha_j) / (1 + 2B - B^2), reduced in
 // FP64 per block and summed on the host in a fixed order.
@@ -148,7 +152,57 @@ __device__ __forceinline__ void load_site(const Params& P, const typename Prec::
 // Pass A at one site x (Site s, linear index idx), from lam*_sa(x) = lam_sa(x + e_a) given by
 // lam_star(c, a): writes X of lam(t), Fbar (D) and the cell-volume densities (NC) at x and sets
 // gt to the site's dL/dgamma terms.
-template <int Q, int NC, class Prec, int PAR, class LamStar>
+// mu = K v for one component's Q values: K = w I + sum over the free rows k of M_k^T lam_k M_k
+// (the forward collision's relaxation, symmetric for the orthogonal basis).
+template <int Q, class R>
+__device__ __forceinline__ void mrt_k_apply(const Params& P, const R (&v)[Q], R (&mu)[Q]) {
+  using L = Lat<Q>;
+  R mk[L::NK];
+  For<0, L::NK>::run([&]<int I>() {
+    constexpr int k = L::krow(I);
+    R m = 0;
+    For<0, Q>::run([&]<int A>() {
+      constexpr int cm = L::m(k, A);
+      if constexpr (cm != 0) m += (R)cm * v[A];
+    });
+    mk[I] = PC<R>::lam(P, I) * m;
+  });
+  const R om = PC<R>::omega(P);
+  For<0, Q>::run([&]<int A>() {
+    R x = om * v[A];
+    For<0, L::NK>::run([&]<int I>() {
+      constexpr int cm = L::m(L::krow(I), A);
+      if constexpr (cm != 0) x += (R)cm * mk[I];
+    });
+    mu[A] = x;
+  });
+}
+
+// Lattice moments m0 = sum_a w_a v_a, m1 = sum_a w_a v_a e_a, m2 = sum_a w_a v_a e_a e_a.
+template <int Q, class R>
+__device__ __forceinline__ void w_moments(const R (&v)[Q], R& m0, R (&m1)[3], R (&m2)[3][3]) {
+  using L = Lat<Q>;
+  m0 = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    m1[d] = 0;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) m2[d][e] = 0;
+  }
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const R lw = (R)L::w(a) * v[a];
+    m0 += lw;
+#pragma unroll
+    for (int d = 0; d < L::D; ++d) {
+      m1[d] += lw * (R)L::e(a, d);
+#pragma unroll
+      for (int e = 0; e < L::D; ++e) m2[d][e] += lw * (R)(L::e(a, d) * L::e(a, e));
+    }
+  }
+}
+
+template <int Q, int NC, class Prec, int PAR, int MRT, class LamStar>
 __device__ __forceinline__ void adj_a_site(const Params& P, const typename Prec::S* __restrict__ f,
                                            const typename Prec::PsiT* __restrict__ psi, const Site& s, int64_t idx,
                                            const LamStar& lam_star, typename Prec::R* __restrict__ X_out,
@@ -194,6 +248,44 @@ __device__ __forceinline__ void adj_a_site(const Params& P, const typename Prec:
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     chi[c] = PC<R>::gamma(P, c) * rc[c] * igs;
+    if constexpr (MRT) {
+      // the feq terms contract with mu = K lam*, the Guo terms with nu = lam* - mu / 2
+      R ls[Q], mu[Q], nu[Q];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) ls[a] = lam_star(c, a);
+      mrt_k_apply<Q, R>(P, ls, mu);
+#pragma unroll
+      for (int a = 0; a < Q; ++a) nu[a] = ls[a] - (R)0.5 * mu[a];
+      R M0, M1[3], M2[3][3], N0, N1[3], N2[3][3];
+      w_moments<Q, R>(mu, M0, M1, M2);
+      w_moments<Q, R>(nu, N0, N1, N2);
+      R M2u[3] = {0, 0, 0}, N2u[3] = {0, 0, 0}, N2F[3] = {0, 0, 0};
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+#pragma unroll
+        for (int e2 = 0; e2 < D; ++e2) {
+          M2u[d] += M2[d][e2] * u[e2];
+          N2u[d] += N2[d][e2] * u[e2];
+          N2F[d] += N2[d][e2] * F[e2];
+        }
+      R M1u = 0, uM2u = 0, N1F = 0, uN2F = 0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        M1u += M1[d] * u[d];
+        uM2u += u[d] * M2u[d];
+        N1F += N1[d] * F[d];
+        uN2F += u[d] * N2F[d];
+      }
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        ub[d] += rc[c] * ((R)3 * M1[d] + (R)9 * M2u[d] - (R)3 * u[d] * M0) +
+                 chi[c] * ((R)-3 * F[d] * N0 + (R)9 * N2F[d]);
+        Fd[d] += chi[c] * ((R)3 * N1[d] - (R)3 * u[d] * N0 + (R)9 * N2u[d]);
+      }
+      chib[c] = (R)3 * N1F - (R)3 * uF * N0 + (R)9 * uN2F;
+      rb[c] = M0 + (R)3 * M1u + (R)4.5 * uM2u - (R)1.5 * uu * M0;
+      continue;
+    }
     R L0 = 0, L1[3] = {0, 0, 0}, L2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
@@ -250,6 +342,23 @@ __device__ __forceinline__ void adj_a_site(const Params& P, const typename Prec:
     jb[d] = ub[d] * irho;
   }
   // X of lam(t); lam* is gathered again (L1)
+  if constexpr (MRT) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      R ls[Q], mu[Q];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) ls[a] = lam_star(c, a);
+      mrt_k_apply<Q, R>(P, ls, mu);
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        R v = ls[a] - mu[a] + rb[c];
+#pragma unroll
+        for (int d = 0; d < D; ++d) v += jb[d] * (R)L::e(a, d);
+        X_out[((int64_t)c * Q + a) * P.N + idx] = v;
+      }
+    }
+    return;
+  }
   const R w1 = (R)1 - om;
 #pragma unroll
   for (int c = 0; c < NC; ++c)
@@ -265,7 +374,7 @@ __device__ __forceinline__ void adj_a_site(const Params& P, const typename Prec:
 // Pass A: collision adjoint at every site x, from lam(t + 1) = X + rbB. Writes X of lam(t),
 // Fbar (D) and the cell-volume densities (NC) per site, and the per-block partial sums of
 // dL/dgamma.
-template <int Q, int NC, class Prec, int PAR>
+template <int Q, int NC, class Prec, int PAR, int MRT>
 __global__ void __launch_bounds__(kAdjBlock) k_adj_a(const Params P, const typename Prec::S* __restrict__ f,
                                                      const typename Prec::PsiT* __restrict__ psi,
                                                      const typename Prec::R* __restrict__ X,
@@ -286,7 +395,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_a(const Params P, const typen
       return X[((int64_t)c * Q + a) * P.N + y] + rbB[(int64_t)c * P.N + y];
     };
     typename Prec::R gt[NC];
-    adj_a_site<Q, NC, Prec, PAR>(P, f, psi, s, idx, lam_star, X_out, Fbar, rho_out, gt);
+    adj_a_site<Q, NC, Prec, PAR, MRT>(P, f, psi, s, idx, lam_star, X_out, Fbar, rho_out, gt);
 #pragma unroll
     for (int c = 0; c < NC; ++c) gg.add(c, gt[c]);
   }
@@ -414,7 +523,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_b(const Params P, const typen
 constexpr int kAbTX = 32, kAbTY = 8;
 static_assert(kAbTX * kAbTY == kAdjBlock, "block_add sums over kAdjBlock threads");
 
-template <int NC, class Prec, int PAR>
+template <int NC, class Prec, int PAR, int MRT>
 __global__ void __launch_bounds__(kAdjBlock)
     k_adj_ab(const Params P, const typename Prec::S* __restrict__ f, const typename Prec::PsiT* __restrict__ psi_t,
              const typename Prec::PsiT* __restrict__ psi_t1, const typename Prec::R* __restrict__ X,
@@ -462,7 +571,7 @@ __global__ void __launch_bounds__(kAdjBlock)
       return X[((int64_t)c * 9 + a) * P.N + yn] + rbs[c][(ly + 1 + L::e(a, 1)) * HX + lx + 1 + L::e(a, 0)];
     };
     R gt[NC];
-    adj_a_site<9, NC, Prec, PAR>(P, f, psi_t, s, idx, lam_star, X_out, F_out, rho_out, gt);
+    adj_a_site<9, NC, Prec, PAR, MRT>(P, f, psi_t, s, idx, lam_star, X_out, F_out, rho_out, gt);
 #pragma unroll
     for (int c = 0; c < NC; ++c) gg.add(c, gt[c]);
   }
@@ -513,7 +622,7 @@ struct AdjFns {  // same layout as the declaration in lbm_capi.cu
   int real_bytes;
 };
 
-template <int Q, int NC, class Prec>
+template <int Q, int NC, class Prec, int MRT>
 struct AdjLaunch {
   using R = typename Prec::R;
   using S = typename Prec::S;
@@ -524,7 +633,7 @@ struct AdjLaunch {
   }
   static void pass_a(const Params& P, const void* f, const void* psi, const void* X, const void* rbB, void* Xo,
                      void* Fb, void* rho, int parity, double* gp, cudaStream_t s) {
-    auto k = parity ? k_adj_a<Q, NC, Prec, 1> : k_adj_a<Q, NC, Prec, 0>;
+    auto k = parity ? k_adj_a<Q, NC, Prec, 1, MRT> : k_adj_a<Q, NC, Prec, 0, MRT>;
     k<<<blocks(P), kAdjBlock, 0, s>>>(P, (const S*)f, (const PsiT*)psi, (const R*)X, (const R*)rbB, (R*)Xo, (R*)Fb,
                                       (R*)rho, gp);
   }
@@ -540,7 +649,7 @@ struct AdjLaunch {
                       const void* Fi, void* Fo, const void* ri, void* ro, void* rbB, int parity, double* gp,
                       double* kp, cudaStream_t s) {
     if constexpr (Q == 9 && LBM_ADJ_FUSED) {
-      auto k = parity ? k_adj_ab<NC, Prec, 1> : k_adj_ab<NC, Prec, 0>;
+      auto k = parity ? k_adj_ab<NC, Prec, 1, MRT> : k_adj_ab<NC, Prec, 0, MRT>;
       k<<<tiles(P), kAdjBlock, 0, s>>>(P, (const S*)f, (const PsiT*)psi_t, (const PsiT*)psi_t1, (const R*)X, (R*)Xo,
                                        (const R*)Fi, (R*)Fo, (const R*)ri, (R*)ro, gp, kp);
     } else {
@@ -558,20 +667,25 @@ struct AdjLaunch {
   }
 };
 
-template <int Q, class Prec>
+template <int Q, class Prec, int MRT>
 const AdjFns* adj_nc(int nc) {
   switch (nc) {
-    case 1: return AdjLaunch<Q, 1, Prec>::table();
-    case 2: return AdjLaunch<Q, 2, Prec>::table();
-    case 3: return AdjLaunch<Q, 3, Prec>::table();
-    case 4: return AdjLaunch<Q, 4, Prec>::table();
+    case 1: return AdjLaunch<Q, 1, Prec, MRT>::table();
+    case 2: return AdjLaunch<Q, 2, Prec, MRT>::table();
+    case 3: return AdjLaunch<Q, 3, Prec, MRT>::table();
+    case 4: return AdjLaunch<Q, 4, Prec, MRT>::table();
   }
   return nullptr;
 }
 
-const AdjFns* adj_fns(int Q, int nc, int precision) {
-  if (Q == 9) return precision == LBM_FP64 ? adj_nc<9, PrecF64>(nc) : adj_nc<9, PrecF32S>(nc);
-  return precision == LBM_FP64 ? adj_nc<19, PrecF64>(nc) : adj_nc<19, PrecF32S>(nc);
+template <int MRT>
+const AdjFns* adj_coll(int Q, int nc, int precision) {
+  if (Q == 9) return precision == LBM_FP64 ? adj_nc<9, PrecF64, MRT>(nc) : adj_nc<9, PrecF32S, MRT>(nc);
+  return precision == LBM_FP64 ? adj_nc<19, PrecF64, MRT>(nc) : adj_nc<19, PrecF32S, MRT>(nc);
+}
+
+const AdjFns* adj_fns(int Q, int nc, int precision, int mrt) {
+  return mrt ? adj_coll<1>(Q, nc, precision) : adj_coll<0>(Q, nc, precision);
 }
 
 }  // namespace lbm

@@ -109,7 +109,7 @@ struct AdjFns {
   unsigned (*rows)(const Params&);  // rows of the partial-sum arrays (one per block of any pass)
   int real_bytes;
 };
-const AdjFns* adj_fns(int Q, int nc, int precision);
+const AdjFns* adj_fns(int Q, int nc, int precision, int mrt);
 }  // namespace lbm
 
 namespace {
@@ -1206,7 +1206,6 @@ lbm_status lbm_restore(lbm_ctx* c, const void* buf, size_t bytes, int64_t t) {
 
 lbm_status lbm_record(lbm_ctx* c, int64_t n, int checkpoint_every) {
   if (!c) return LBM_ERR_ARG;
-  if (c->collision != LBM_BGK) return fail(c, LBM_ERR_ARG, "the adjoint covers the BGK collision only");
   if (c->P.split != LBM_SPLIT_VOLATILITY)
     return fail(c, LBM_ERR_ARG, "the adjoint covers the volatility split (Eq. distributionforce) only");
   if (n < 1 || checkpoint_every < 1) return fail(c, LBM_ERR_ARG, "n and checkpoint_every must be >= 1");
@@ -1336,7 +1335,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, const double* drho, double* dkij, double* dga
   if (!c || !drho) return c ? fail(c, LBM_ERR_ARG, "drho is NULL") : LBM_ERR_ARG;
   if (c->rec_t0 < 0 || c->rec_t0 + c->rec_n != c->t)
     return fail(c, LBM_ERR_ARG, "no recording ends at the current step (call lbm_record)");
-  const lbm::AdjFns* A = lbm::adj_fns(c->Q, c->nc, c->precision);
+  const lbm::AdjFns* A = lbm::adj_fns(c->Q, c->nc, c->precision, c->collision == LBM_MRT);
   const int64_t N = c->P.N;
   const int nc = c->nc, Q = c->Q, K = c->ck_every;
   const size_t sbytes = lbm_state_bytes(c), lbytes = (size_t)nc * Q * N * A->real_bytes;
