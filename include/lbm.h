@@ -207,6 +207,23 @@ lbm_status lbm_restore(lbm_ctx *ctx, const void *buf, size_t bytes, int64_t t);
  * and needs no co-resident launch. Failures are reported as on the trailing path. The same
  * Section 3.4 step as every other path, bit for bit. */
 enum { LBM_PATH_AUTO = 0, LBM_PATH_TWO_KERNEL = 1, LBM_PATH_FUSED = 2, LBM_PATH_TRAILING = 3, LBM_PATH_QUEUE = 4 };
+/* The schedule LBM_PATH_QUEUE runs on an nx x ny x nz grid (host arithmetic only, no device;
+ * exported so that it can be checked without a GPU). The dependency it encodes is that of
+ * Section 3.4's step: psi at a site needs the densities of the state after the collisions of
+ * its neighbours. Each z plane is cut into nch chunks of `chunk` consecutive sites of the
+ * x-fastest plane index (chunk <= 0: the library's 512). Outputs, each skipped when NULL:
+ *   nbr[nch * LBM_QUEUE_MAX_NBR]: per chunk, the other chunks that hold in-plane neighbours
+ *     (periodic, the 8 of the D3Q19 stencil's plane projection) of its sites, -1 padded;
+ *   tasks[2 * nz * nch]: the ticket order. The collision of chunk c of plane z is z*nch + c;
+ *     psi of the next step over that chunk is -(z*nch + c) - 1. Every collision appears in
+ *     plane order, and each psi task follows the collision of chunk c of plane z + 1 + lag
+ *     (lag <= 0: the library's 6). The psi tasks the march does not place come last, plane 0
+ *     at the very end. Every collision a psi task needs (planes z - 1 .. z + 1 of the chunk
+ *     and its neighbour chunks) has a smaller ticket.
+ * Returns nch, or -1 when the grid is not served (nx or ny < 1, nz < 3, a chunk with more
+ * than LBM_QUEUE_MAX_NBR neighbour chunks). Call it with NULL outputs first to size them. */
+#define LBM_QUEUE_MAX_NBR 16
+int lbm_queue_schedule(int nx, int ny, int nz, int chunk, int lag, int *nbr, int *tasks);
 lbm_status lbm_set_path(lbm_ctx *ctx, int path);
 /* The path lbm_step takes now (LBM_PATH_TWO_KERNEL, LBM_PATH_FUSED, LBM_PATH_TRAILING or
  * LBM_PATH_QUEUE). */

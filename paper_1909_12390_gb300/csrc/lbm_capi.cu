@@ -509,6 +509,72 @@ bool setup_trail3(lbm_ctx* c) {
   return true;
 }
 
+// The task-queue step's schedule (host arithmetic only): chunks of TS consecutive sites of
+// the flattened (y, x) index of a plane; nbr[c * kF3MaxNbr ..] the chunks holding the in-plane
+// neighbours of chunk c's sites (-1 padded); tasks the ticket order (collision of chunk c of
+// plane z: z nch + c; psi of the next step there: -(z nch + c) - 1), every collision in plane
+// order with the psi task of (z, c) after the collision of (z + 1 + lag, c) and the psi tasks
+// the march does not place (planes nz - 1 and 0 among them) at the end, plane 0 last. Checks
+// that every collision a psi task needs (planes z - 1 .. z + 1 of the chunk and its neighbour
+// chunks) has a smaller ticket. Returns the chunks per plane, or -1 for a grid it does not serve.
+int queue_schedule(int nx, int ny, int nz, int TS, int lag, std::vector<int>& nbr, std::vector<int>& tasks) {
+  const long long nxy = (long long)nx * ny;
+  if (nx < 1 || ny < 1 || nz < 3 || TS < 1 || lag < 1) return -1;
+  const int nch = (int)((nxy + TS - 1) / TS);
+  if ((long long)nch * nz * 2 >= (1LL << 30)) return -1;
+  const int K = lbm::kF3MaxNbr;
+  nbr.assign((size_t)nch * K, -1);
+  for (int ch = 0; ch < nch; ++ch) {
+    int n = 0;
+    const long long hi = std::min<long long>((long long)(ch + 1) * TS, nxy);
+    for (long long i = (long long)ch * TS; i < hi; ++i) {
+      const int x = (int)(i % nx), y = (int)(i / nx);
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int o = (int)((((long long)((y + dy + ny) % ny)) * nx + (x + dx + nx) % nx) / TS);
+          if (o == ch) continue;
+          bool seen = false;
+          for (int k = 0; k < n; ++k) seen = seen || nbr[(size_t)ch * K + k] == o;
+          if (seen) continue;
+          if (n == K) return -1;
+          nbr[(size_t)ch * K + n++] = o;
+        }
+    }
+  }
+  const long long ncol = (long long)nz * nch;
+  tasks.clear();
+  tasks.reserve((size_t)(2 * ncol));
+  std::vector<char> placed((size_t)ncol, 0);
+  for (long long i = 0; i < ncol; ++i) {
+    tasks.push_back((int)i);
+    const long long zp = i / nch - 1 - lag, cp = i % nch;
+    if (zp >= 1 && zp <= nz - 2) {
+      tasks.push_back((int)(-(zp * nch + cp) - 1));
+      placed[(size_t)(zp * nch + cp)] = 1;
+    }
+  }
+  for (int z = 1; z < nz; ++z)
+    for (int ch = 0; ch < nch; ++ch)
+      if (!placed[(size_t)z * nch + ch]) tasks.push_back(-(z * nch + ch) - 1);
+  for (int ch = 0; ch < nch; ++ch) tasks.push_back(-ch - 1);
+  std::vector<long long> pos((size_t)ncol, -1);
+  for (size_t p = 0; p < tasks.size(); ++p)
+    if (tasks[p] >= 0) pos[(size_t)tasks[p]] = (long long)p;
+  for (size_t p = 0; p < tasks.size(); ++p) {
+    if (tasks[p] >= 0) continue;
+    const int q = -tasks[p] - 1, z = q / nch, ch = q % nch;
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int zz = (z + dz + nz) % nz;
+      for (int j = -1; j < K && (j < 0 || nbr[(size_t)ch * K + j] >= 0); ++j) {
+        const int cc = j < 0 ? ch : nbr[(size_t)ch * K + j];
+        const long long pc = pos[(size_t)zz * nch + cc];
+        if (pc < 0 || pc >= (long long)p) return -1;
+      }
+    }
+  }
+  return nch;
+}
+
 // The task-queue one-pass step (k_trailq, D3Q19): each plane cut into nch chunks of
 // ops->trailq_chunk consecutive sites of the flattened (y, x) index; per chunk the chunks
 // holding the in-plane neighbours of its sites; the ticket order of the step's tasks (every
@@ -525,61 +591,10 @@ bool setup_trailq(lbm_ctx* c) {
   const int cap = c->ops->trailq_max_blocks();
   if (cap <= 0) return false;
   const int TS = (int)std::min<long long>(c->ops->trailq_chunk, nxy);
-  const int nch = (int)((nxy + TS - 1) / TS);
-  if ((long long)nch * nz * 2 >= (1LL << 30)) return false;
-  const int K = lbm::kF3MaxNbr;
-  std::vector<int> nbr((size_t)nch * K, -1);
-  for (int ch = 0; ch < nch; ++ch) {
-    int n = 0;
-    const long long hi = std::min<long long>((long long)(ch + 1) * TS, nxy);
-    for (long long i = (long long)ch * TS; i < hi; ++i) {
-      const int x = (int)(i % nx), y = (int)(i / nx);
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int o = (int)((((long long)((y + dy + ny) % ny)) * nx + (x + dx + nx) % nx) / TS);
-          if (o == ch) continue;
-          bool seen = false;
-          for (int k = 0; k < n; ++k) seen = seen || nbr[(size_t)ch * K + k] == o;
-          if (seen) continue;
-          if (n == K) return false;
-          nbr[(size_t)ch * K + n++] = o;
-        }
-    }
-  }
-  // ticket order
-  const int lag = c->ops->trailq_lag;
+  std::vector<int> nbr, tasks;
+  const int nch = queue_schedule(nx, ny, nz, TS, c->ops->trailq_lag, nbr, tasks);
+  if (nch < 0) return false;
   const long long ncol = (long long)nz * nch;
-  std::vector<int> tasks;
-  tasks.reserve((size_t)(2 * ncol));
-  std::vector<char> placed((size_t)ncol, 0);
-  for (long long i = 0; i < ncol; ++i) {
-    tasks.push_back((int)i);
-    const long long zp = i / nch - 1 - lag, cp = i % nch;
-    if (zp >= 1 && zp <= nz - 2) {
-      tasks.push_back((int)(-(zp * nch + cp) - 1));
-      placed[(size_t)(zp * nch + cp)] = 1;
-    }
-  }
-  for (int z = 1; z < nz; ++z)
-    for (int ch = 0; ch < nch; ++ch)
-      if (!placed[(size_t)z * nch + ch]) tasks.push_back(-(z * nch + ch) - 1);
-  for (int ch = 0; ch < nch; ++ch) tasks.push_back(-ch - 1);
-  // every collision a psi task needs has a smaller ticket
-  std::vector<long long> pos((size_t)ncol, -1);
-  for (size_t p = 0; p < tasks.size(); ++p)
-    if (tasks[p] >= 0) pos[(size_t)tasks[p]] = (long long)p;
-  for (size_t p = 0; p < tasks.size(); ++p) {
-    if (tasks[p] >= 0) continue;
-    const int q = -tasks[p] - 1, z = q / nch, ch = q % nch;
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int zz = (z + dz + nz) % nz;
-      for (int j = -1; j < K && (j < 0 || nbr[(size_t)ch * K + j] >= 0); ++j) {
-        const int cc = j < 0 ? ch : nbr[(size_t)ch * K + j];
-        const long long pc = pos[(size_t)zz * nch + cc];
-        if (pc < 0 || pc >= (long long)p) return false;
-      }
-    }
-  }
   lbm::FusedArgs a{};
   a.mode = 5;
   a.G = (int)std::min<long long>(cap, (long long)tasks.size());
@@ -1309,6 +1324,21 @@ int64_t revolve_count(int64_t n, int s) {
   if (s == 0) return n * (n - 1) / 2;
   const int64_t m = binomial_split(n, s);
   return m + revolve_count(n - m, s - 1) + revolve_count(m, s);
+}
+
+static_assert(lbm::kF3MaxNbr == LBM_QUEUE_MAX_NBR, "neighbour-chunk list length of lbm_queue_schedule");
+
+int lbm_queue_schedule(int nx, int ny, int nz, int chunk, int lag, int* nbr, int* tasks) {
+  if (nx < 1 || ny < 1) return -1;
+  if (chunk <= 0) chunk = lbm::kTQChunk;
+  if (lag <= 0) lag = lbm::kTQLag;
+  const int TS = (int)std::min<long long>(chunk, (long long)nx * ny);
+  std::vector<int> nb, tk;
+  const int nch = queue_schedule(nx, ny, nz, TS, lag, nb, tk);
+  if (nch < 0) return -1;
+  if (nbr) std::copy(nb.begin(), nb.end(), nbr);
+  if (tasks) std::copy(tk.begin(), tk.end(), tasks);
+  return nch;
 }
 
 int64_t lbm_revolve_steps(int64_t n, int snapshots) {

@@ -28,7 +28,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_init", "lbm_step"
            "lbm_step_static", "lbm_step_static_error", "lbm_batch_create", "lbm_batch_destroy",
            "lbm_batch_init", "lbm_batch_step", "lbm_batch_case_status", "lbm_batch_fields",
            "lbm_batch_get_f", "lbm_batch_tune", "lbm_batch_tune_report", "lbm_batch_sites",
-           "lbm_batch_last_error", "lbm_record", "lbm_adjoint", "lbm_set_adjoint_memory", "lbm_test_adjoint_overlap", "lbm_revolve_steps", "lbm_flash", "lbm_flash_error", "lbm_diagnostics")
+           "lbm_batch_last_error", "lbm_record", "lbm_adjoint", "lbm_set_adjoint_memory", "lbm_test_adjoint_overlap", "lbm_revolve_steps", "lbm_queue_schedule", "lbm_flash", "lbm_flash_error", "lbm_diagnostics")
 STATIC_MAX_SITES = 1048576
 PATH_AUTO, PATH_TWO_KERNEL, PATH_FUSED, PATH_TRAILING, PATH_QUEUE = 0, 1, 2, 3, 4
 FUSED_TILES, FUSED_PLANES = 1, 3
@@ -152,6 +152,8 @@ def lib() -> ctypes.CDLL:
         L.lbm_test_adjoint_overlap.argtypes = [vp, ctypes.c_int]
         L.lbm_revolve_steps.argtypes = [ctypes.c_int64, ctypes.c_int]
         L.lbm_revolve_steps.restype = ctypes.c_int64
+        L.lbm_queue_schedule.argtypes = [ctypes.c_int] * 5 + [vp, vp]
+        L.lbm_queue_schedule.restype = ctypes.c_int
         L.lbm_last_error.argtypes = [vp]
         L.lbm_last_error.restype = ctypes.c_char_p
         L.lbm_scale_to_lattice.argtypes = [ctypes.c_int, ctypes.POINTER(Component), ctypes.c_double,
@@ -195,6 +197,23 @@ def make_args(shape, components, T, gamma=None, kij=None, beta=1.0, G=-1.0, coll
               gamma=arr(gamma, nc), beta=beta, G=G, collision=collision,
               mrt_rates=arr(mrt_rates, Q), precision=precision, rho_ref=arr(rho_ref, nc), split=int(split))
     return Grid(nx, ny, nz, Q), comps, eos, keep
+
+
+QUEUE_MAX_NBR = 16
+
+
+def queue_schedule(nx: int, ny: int, nz: int, chunk: int = 0, lag: int = 0):
+    """lbm_queue_schedule: (nch, nbr[nch, QUEUE_MAX_NBR], tasks[2 nz nch]) of the task-queue
+    step on an nx x ny x nz grid, or None when the grid is not served."""
+    L = lib()
+    nch = int(L.lbm_queue_schedule(nx, ny, nz, chunk, lag, None, None))
+    if nch < 0:
+        return None
+    nbr = np.empty((nch, QUEUE_MAX_NBR), dtype=np.int32)
+    tasks = np.empty(2 * nz * nch, dtype=np.int32)
+    L.lbm_queue_schedule(nx, ny, nz, chunk, lag, nbr.ctypes.data_as(ctypes.c_void_p),
+                         tasks.ctypes.data_as(ctypes.c_void_p))
+    return nch, nbr, tasks
 
 
 def revolve_steps(n: int, snapshots: int) -> int:
