@@ -5,7 +5,8 @@ with the binary interaction coefficient of the pair spec["pair"] set to `zeta` a
 volatility coefficients gamma_i (i != least volatile) scaled by `s`, and returns the final
 cell-volume densities (nc, *grid) as a float64 CPU tensor. Its backward runs the library's
 hand-written adjoint with checkpoints every spec["checkpoint_every"] steps and returns dL/dzeta
-and dL/ds.
+and dL/ds. spec["collision"] (lbm.BGK, the default, or lbm.MRT with spec["mrt_rates"]) selects
+the collision.
 """
 from __future__ import annotations
 
@@ -45,6 +46,7 @@ class LatticeRun(torch.autograd.Function):
         g, g0, h = _gamma(spec, s.item())
         lat = lbm.Lattice(tuple(spec["shape"]), spec["components"], T=spec["T"], tau=spec["tau"], gamma=g,
                           kij=_kij(spec, zeta.item()), beta=spec["beta"], G=spec.get("G", -1.0),
+                          collision=spec.get("collision", lbm.BGK), mrt_rates=spec.get("mrt_rates"),
                           precision=spec.get("precision", lbm.FP32_SHIFTED))
         lat.init(spec["rho0"])
         lat.record(spec["steps"], spec.get("checkpoint_every", 55))

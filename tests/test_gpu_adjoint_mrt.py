@@ -144,3 +144,26 @@ def test_mrt_adjoint_fp32_matches_fp64_oracle(cases):
           % (dk[0, 1] + dk[1, 0], ok12, dgam[0] * c["gamma"][0], os_))
     assert dk[0, 1] + dk[1, 0] == pytest.approx(ok12, rel=2e-3)
     assert dgam[0] * c["gamma"][0] == pytest.approx(os_, rel=2e-3)
+
+
+def test_mrt_autograd_function_matches_oracle_duals(cases):
+    """LatticeRun with the MRT collision: dL/dzeta_12 and dL/ds through torch's backward equal
+    the oracle's MRT dual numbers (FP64)."""
+    import torch
+    from paper_1909_12390_gb300 import lbm
+    from paper_1909_12390_gb300.autograd import LatticeRun
+    c = _mixture(cases, 9)
+    shape, steps, k12 = (32, 24), 24, 0.01
+    rho0, w = _setup(c, shape)
+    spec = dict(shape=shape, components=comps_of(c), T=c["T"], tau=c["tau"], gamma=c["gamma"], beta=c["beta"],
+                G=c["G"], collision=lbm.MRT, mrt_rates=c["mrt_s"], precision=FP64, rho0=rho0, steps=steps,
+                checkpoint_every=8)
+    zeta = torch.tensor(k12, dtype=torch.float64, requires_grad=True)
+    s = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    rho = LatticeRun.apply(zeta, s, spec)
+    loss = 0.5 * (torch.from_numpy(w) * rho * rho).sum()
+    loss.backward()
+    Lo, ok12, os_, _ = _oracle_grads(c, shape, rho0, w, k12, 1.0, steps)
+    assert float(loss) == pytest.approx(Lo, rel=1e-11)
+    assert float(zeta.grad) == pytest.approx(ok12, rel=1e-8)
+    assert float(s.grad) == pytest.approx(os_, rel=1e-8)
