@@ -99,3 +99,20 @@ def test_flash_rejects_bad_arguments_before_any_device_work():
     assert ei.value.status == lbm.ERR_ARG
     r = lbm.flash(comps, [], [], np.zeros((0, 2)))                     # no cases: nothing to do
     assert r["V"].shape == (0,)
+
+
+def test_binding_constants_equal_the_header():
+    """Every enumerator and numeric #define of include/lbm.h that the Python binding repeats
+    (LBM_X -> lbm.X) has the header's value, and the status codes and step paths are all
+    repeated."""
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"\bLBM_([A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+    consts.update({m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+LBM_([A-Z0-9_]+)\s+(-?\d+)", src)})
+    for name in ("OK", "ERR_ARG", "ERR_CUDA", "ERR_OOM", "ERR_PSI_DOMAIN", "ERR_NONFINITE", "ERR_TIMEOUT",
+                 "PATH_AUTO", "PATH_TWO_KERNEL", "PATH_FUSED", "PATH_TRAILING", "PATH_QUEUE"):
+        assert name in consts and hasattr(lbm, name), name
+    checked = [n for n in consts if hasattr(lbm, n)]
+    assert len(checked) >= 20
+    for name in checked:
+        assert getattr(lbm, name) == consts[name], name
