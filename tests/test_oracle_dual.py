@@ -4,7 +4,7 @@ split factors, against what the mathematics fixes rather than against the oracle
 * the dual-number derivative of a run equals central finite differences of the plain FP64
   step (oracle.step), for the binary interaction coefficient zeta_12 (Eq. randommixingrule),
   the split-factor scale s (gamma_i -> s gamma_i, Eq. distributionforce) and a perturbation
-  of the initial populations, with BGK and MRT collisions;
+  of the initial populations, with BGK and MRT collisions (D2Q9, and D3Q19 with MRT);
 * the two derivative directions are independent: swapping the seeds swaps the results
   bit for bit, and a seed scaled by two gives exactly twice the derivative;
 * with identical components the total density obeys the single-fluid LBE whatever the split
@@ -87,6 +87,42 @@ def test_dual_derivatives_equal_central_differences(cases, collision):
     for d in range(2):
         scale = np.max(np.abs(df[d]))
         assert scale > 1e-6  # the derivative is not trivially zero
+        err = np.max(np.abs(df[d] - fd[d])) / scale
+        assert err < 1e-6, (d, err)
+
+
+def test_dual_derivatives_equal_central_differences_d3q19_mrt(cases):
+    """The same pin on D3Q19 with the MRT collision and three components (the sphere
+    workload's mixture and rates) on a 4 x 4 x 4 grid. Here d f / d zeta_12 is about 2e-4 of
+    the populations, so h = 1e-6 leaves the difference to rounding (2.8e-6 relative, falling as
+    1 / h); h = 1e-4 gives 3e-8."""
+    c = cases["c3"]
+    nc = len(c["gamma"])
+    k12, steps, h = 0.01, 6, 1e-4
+    kij = np.zeros((nc, nc))
+    kij[0, 1] = kij[1, 0] = k12
+    base = _case(c, (4, 4, 4), Q=19, collision=1, s=list(c["mrt_s"]), kij=kij.tolist())
+    f0 = _droplet(base, c, radius=1.4, width=1.5)
+    g0 = np.array(c["gamma"], dtype=float)
+    hv = int(c["least_volatile"])
+    dk, dg = _seeds(nc, hv, g0)
+    f, df = oracle.step_dual(base, f0, np.zeros((2,) + f0.shape), dk, dg, steps)
+    assert np.array_equal(f, oracle.step(base, f0, steps))
+
+    def run_zeta(z):
+        k = kij.copy()
+        k[0, 1] = k[1, 0] = z
+        return oracle.step(_with(base, kij=k.tolist()), f0, steps)
+
+    def run_s(s):
+        g = g0.copy()
+        g[np.arange(nc) != hv] *= s
+        return oracle.step(_with(base, gamma=list(g)), f0, steps)
+
+    fd = [(run_zeta(k12 + h) - run_zeta(k12 - h)) / (2 * h), (run_s(1 + h) - run_s(1 - h)) / (2 * h)]
+    for d in range(2):
+        scale = np.max(np.abs(df[d]))
+        assert scale > 1e-8
         err = np.max(np.abs(df[d] - fd[d])) / scale
         assert err < 1e-6, (d, err)
 
